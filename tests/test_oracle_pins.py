@@ -1,0 +1,555 @@
+"""Pins of the FP64 CPU oracle against facts independent of it.
+
+Every check here compares the oracle with something it does not compute
+itself: high-precision quadrature of the paper's c1..c5, closed-form moments
+of Maxwellians, Gauss-Hermite integration of the unreduced Shakhov
+distribution, Venkatakrishnan's function at known points, exactness of
+least squares on linear data, analytic derivatives of the Maxwellian and the
+Euler equations, textbook upwind schemes in the free-molecular limit, the
+closed-form relaxation of the trapezoid collision update, and conservation
+invariants of the finite-volume form.
+"""
+import math
+
+import mpmath
+import numpy as np
+import pytest
+from scipy.special import erfc
+
+import oracle
+from paper_2412_06546_gb300 import cases as cs
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.4: time integrals of c1..c5
+# --------------------------------------------------------------------------
+def _quad_c(dt, tau):
+    mpmath.mp.dps = 40
+    dt = mpmath.mpf(dt)
+    tau = mpmath.mpf(tau)
+    e = lambda t: mpmath.e ** (-t / tau)
+    cs_ = [lambda t: e(t),
+           lambda t: -t * e(t),
+           lambda t: 1 - e(t),
+           lambda t: t * e(t) - tau * (1 - e(t)),
+           lambda t: t - tau * (1 - e(t))]
+    return [float(mpmath.quad(c, [0, dt])) for c in cs_]
+
+
+@pytest.mark.parametrize("x", [1e-8, 1e-4, 1e-2, 0.3, 0.4999, 0.5, 0.5001, 1.0, 3.0, 30.0, 1e3])
+def test_time_integrals_match_quadrature(x):
+    dt = 0.013
+    tau = dt / x
+    got = oracle.time_integrals(dt, tau)
+    ref = _quad_c(dt, tau)
+    for i in range(5):
+        scale = dt if i in (0, 2) else dt * dt
+        assert abs(got[i] - ref[i]) <= 1e-12 * max(abs(ref[i]), 1e-12 * scale), (i, got[i], ref[i])
+
+
+def test_time_integrals_free_molecular_limit():
+    dt = 0.02
+    q = oracle.time_integrals(dt, float("inf"))
+    assert q[0] == dt and q[1] == -0.5 * dt * dt
+    assert q[2] == 0.0 and q[3] == 0.0 and q[4] == 0.0
+
+
+def test_time_integrals_continuum_limit():
+    # tau -> 0: free transport vanishes, q3 -> dt, q4 -> 0, q5 -> dt^2/2
+    dt = 0.02
+    q = oracle.time_integrals(dt, 1e-12)
+    assert abs(q[0]) < 1e-11 and abs(q[1]) < 1e-11
+    assert abs(q[2] - dt) < 1e-11 and abs(q[3]) < 1e-11 and abs(q[4] - 0.5 * dt * dt) < 1e-11
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.1-2.3: Maxwellian, Shakhov terms, discrete moments
+# --------------------------------------------------------------------------
+def _conserved(D, rho, U, T):
+    return np.array([rho] + [rho * u for u in U] + [rho * (0.5 * np.dot(U, U) + 1.5 * T)])
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_discrete_maxwellian_moments(D):
+    rho, T = 1.7, 1.3
+    U = np.array([0.7, -0.4, 0.25])[:D]
+    if D == 2:
+        vg = cs.cartesian_vgrid((121, 121), (-12, -12), (12, 12))
+    else:
+        vg = cs.cartesian_vgrid((49, 49, 49), (-10, -10, -10), (10, 10, 10))
+    u, w = vg["u"], vg["w"]
+    H, B = oracle.maxwellian(D, rho, U, 1.0 / (2 * T), u)
+    if D == 3:
+        assert np.all(B == 0.0)
+    W = np.array([np.sum(w * H)] + [np.sum(w * u[:, d] * H) for d in range(D)]
+                 + [0.5 * np.sum(w * (np.sum(u * u, 1) * H + B))])
+    assert np.allclose(W, _conserved(D, rho, U, T), rtol=1e-11, atol=0)
+    q = oracle.heat_flux(D, u, w, H, B if D == 2 else None, U)
+    assert np.abs(q).max() < 1e-11
+
+
+def test_shakhov_reduction_matches_xi_integral():
+    """H+ and B+ of Sec. 2.2 equal int g+ dxi and int xi^2 g+ dxi of the
+    unreduced Shakhov distribution (2D: one internal translational dof)."""
+    D, Pr = 2, 2.0 / 3.0
+    rho, T = 1.3, 0.8
+    lam = 1 / (2 * T)
+    U = np.array([0.3, -0.2])
+    q = np.array([0.11, -0.07])
+    p = rho * T
+    u = np.array([[0.1, 0.2], [1.5, -0.7], [-2.0, 0.4], [0.0, 3.0]])
+    Hp, Bp = oracle.shakhov(D, Pr, rho, U, lam, q, u)
+    xg, wg = np.polynomial.hermite.hermgauss(12)   # int e^{-x^2} P(x) dx
+    for k in range(len(u)):
+        c = u[k] - U
+        xi = xg / math.sqrt(lam)
+        g = rho * (lam / math.pi) ** 1.5 * np.exp(-lam * c @ c)   # times e^{-lam xi^2}
+        c2f = c @ c + xi ** 2
+        gplus = g * (1 - Pr) * (c @ q) * (c2f / T - 5) / (5 * p * T)
+        Hp_ref = np.sum(wg * gplus) / math.sqrt(lam)
+        Bp_ref = np.sum(wg * xi ** 2 * gplus) / math.sqrt(lam)
+        assert abs(Hp[k] - Hp_ref) <= 1e-13 * max(1.0, abs(Hp_ref))
+        assert abs(Bp[k] - Bp_ref) <= 1e-13 * max(1.0, abs(Bp_ref))
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_shakhov_heat_flux_is_one_minus_Pr_q(D):
+    """The Shakhov equilibrium carries heat flux (1-Pr) q and no mass,
+    momentum or energy beyond the Maxwellian."""
+    Pr = 2.0 / 3.0
+    rho, T = 1.1, 1.4
+    lam = 1 / (2 * T)
+    U = np.array([0.4, -0.3, 0.2])[:D]
+    q = np.array([0.09, 0.05, -0.04])[:D]
+    if D == 2:
+        vg = cs.cartesian_vgrid((121, 121), (-13, -13), (13, 13))
+    else:
+        vg = cs.cartesian_vgrid((51, 51, 51), (-11, -11, -11), (11, 11, 11))
+    u, w = vg["u"], vg["w"]
+    H, B = oracle.maxwellian(D, rho, U, lam, u)
+    Hp, Bp = oracle.shakhov(D, Pr, rho, U, lam, q, u)
+    qq = oracle.heat_flux(D, u, w, H + Hp, (B + Bp) if D == 2 else None, U)
+    assert np.allclose(qq, (1 - Pr) * q, rtol=0, atol=1e-10)
+    u2 = np.sum(u * u, 1)
+    assert abs(np.sum(w * Hp)) < 1e-11
+    for d in range(D):
+        assert abs(np.sum(w * u[:, d] * Hp)) < 1e-11
+    assert abs(0.5 * np.sum(w * (u2 * Hp + Bp))) < 1e-11
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.1 Step 2: least squares and the Venkatakrishnan limiter
+# --------------------------------------------------------------------------
+def test_venkatakrishnan_function_values():
+    v = oracle.venkat
+    assert v(1.0, 1.0, 0.0) == pytest.approx(0.75, rel=1e-15)     # y = 1
+    assert v(2.0, 1.0, 0.0) == pytest.approx(1.0, rel=1e-15)      # y = 2
+    assert v(0.0, 1.0, 0.0) == 0.0                                # y = 0
+    assert v(-1.0, -1.0, 0.0) == pytest.approx(0.75, rel=1e-15)   # odd symmetry
+    assert v(0.3, 0.0, 0.1) == 1.0                                # flat slope
+    assert v(1e-9, 1e-3, 1.0) == pytest.approx(1.0, rel=1e-5)     # large eps: inactive
+    for y in np.linspace(0, 2, 21):
+        assert 0.0 <= v(y, 1.0, 1e-3) <= 1.0 + 1e-15
+
+
+def _ghost_points(mesh):
+    x, fc, fx, fn = mesh["cell_xc"], mesh["face_cells"], mesh["face_xc"], mesh["face_n"]
+    own = x[fc[:, 0]]
+    rn = np.sum((fx - own) * fn, 1)
+    return own + 2 * rn[:, None] * fn
+
+
+def test_least_squares_exact_on_linear_fields():
+    case = cs.cylinder_case(n_cells=1500, nvx=4, nvy=4)
+    mesh = case["mesh"]
+    o = oracle.OracleCase(mesh, case["vgrid"], case["params"], case["init"])
+    a = np.array([0.37, -1.21])
+    phi = mesh["cell_xc"] @ a + 0.5
+    ghost = _ghost_points(mesh) @ a + 0.5
+    g = o.scalar_gradient(phi, ghost, limited=False)
+    assert np.abs(g - a).max() < 1e-11
+    gl = o.scalar_gradient(phi, ghost, limited=True)
+    ratio = gl @ a / (a @ a)
+    assert ratio.min() >= -1e-15 and ratio.max() <= 1 + 1e-13
+    assert np.abs(gl - ratio[:, None] * a).max() < 1e-11
+
+
+def test_least_squares_exact_3d():
+    mesh = cs.hex_mesh(4, 3, 5, 1.0, 0.8, 1.2)
+    vg = cs.cartesian_vgrid((3, 3, 3), (-1, -1, -1), (1, 1, 1))
+    pr = cs.params(0.1, walls=[{"T": 1.0, "U": [0, 0, 0]}])
+    o = oracle.OracleCase(mesh, vg, pr, cs.uniform_state(60, 3))
+    a = np.array([0.2, -0.5, 0.9])
+    g = o.scalar_gradient(mesh["cell_xc"] @ a, None, limited=False)
+    assert np.abs(g - a).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.4: interface equilibrium, spatial and time slopes of g0
+# --------------------------------------------------------------------------
+def _fine_grid(D):
+    if D == 2:
+        return cs.cartesian_vgrid((141, 141), (-14, -14), (14, 14))
+    return cs.cartesian_vgrid((57, 57, 57), (-12, -12, -12), (12, 12, 12))
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_equilibrium_of_equal_states_is_the_state(D):
+    vg = _fine_grid(D)
+    W = _conserved(D, 1.2, np.array([0.5, -0.3, 0.1])[:D], 0.9)
+    n = np.zeros(D)
+    n[0] = 0.6
+    n[1] = 0.8
+    W0, a, A = oracle.face_equilibrium(D, vg["u"], vg["w"], n, W, W, np.zeros((D, D + 2)))
+    assert np.allclose(W0, W, rtol=1e-11, atol=0)
+    assert np.abs(a).max() < 1e-10 and np.abs(A).max() < 1e-10
+
+
+def _half_range(rho, U, T, sign):
+    """Analytic moments of a 2D Maxwellian (plus one internal dof) over u_x > 0
+    (sign=+1) or u_x < 0 (sign=-1): the classic gas-kinetic half-range integrals."""
+    lam = 1 / (2 * T)
+    s = math.sqrt(lam)
+    Ux, Uy = U
+    m0 = 0.5 * erfc(-sign * s * Ux)
+    m1 = Ux * m0 + sign * math.exp(-lam * Ux * Ux) / (2 * math.sqrt(math.pi * lam))
+    m2 = (Ux * Ux + 1 / (2 * lam)) * m0 + sign * Ux * math.exp(-lam * Ux * Ux) / (2 * math.sqrt(math.pi * lam))
+    # energy: 1/2 (u_x^2 + u_y^2 + xi^2): <u_y^2> = Uy^2 + T, <xi^2> = T
+    return rho * np.array([m0, m1, Uy * m0, 0.5 * (m2 + (Uy * Uy + T) * m0 + T * m0)])
+
+
+def test_half_range_equilibrium_matches_erfc_moments():
+    """W0 of two different face states converges (Richardson in the grid
+    spacing) to the analytic half-range moments."""
+    WLp = (1.3, np.array([0.4, 0.2]), 1.2)
+    WRp = (0.8, np.array([-0.3, 0.1]), 0.7)
+    ref = _half_range(*WLp, +1) + _half_range(*WRp, -1)
+    WL = _conserved(2, WLp[0], WLp[1], WLp[2])
+    WR = _conserved(2, WRp[0], WRp[1], WRp[2])
+    est = []
+    for m in (40, 80, 160):
+        vg = cs.cartesian_vgrid((2 * m + 1, 2 * m + 1), (-12, -12), (12, 12))
+        W0, _, _ = oracle.face_equilibrium(2, vg["u"], vg["w"], np.array([1.0, 0.0]), WL, WR,
+                                           np.zeros((2, 4)))
+        est.append(W0)
+    r1 = (4 * est[1] - est[0]) / 3
+    r2 = (4 * est[2] - est[1]) / 3
+    rich = (16 * r2 - r1) / 15
+    assert np.abs(rich - ref).max() < 1e-8, (rich, ref)   # O(h^6) remainder
+    assert np.abs(est[2] - ref).max() < 1e-3   # plain grid error O(h^2)
+
+
+def _slope_map(D, W, dW):
+    """Coefficients (a0, a_u, a_E) with (a.psi) g = dg for the Maxwellian g of W
+    and a variation dW of the conserved variables (chain rule on ln g)."""
+    rho = W[0]
+    U = W[1:1 + D] / rho
+    E = W[D + 1] / rho
+    T = (2 / 3) * (E - 0.5 * U @ U)
+    lam = 1 / (2 * T)
+    drho = dW[0]
+    dU = (dW[1:1 + D] - U * drho) / rho
+    dE = (dW[D + 1] - E * drho) / rho
+    dT = (2 / 3) * (dE - U @ dU)
+    dlam = -dT / (2 * T * T)
+    a0 = drho / rho + 1.5 * dlam / lam - dlam * (U @ U) - 2 * lam * (U @ dU)
+    au = 2 * U * dlam + 2 * lam * dU
+    return np.concatenate([[a0], au, [-2 * dlam]])
+
+
+def _euler_flux(D, W, d):
+    rho = W[0]
+    U = W[1:1 + D] / rho
+    E = W[D + 1] / rho
+    p = rho * (2 / 3) * (E - 0.5 * U @ U)
+    F = np.zeros(D + 2)
+    F[0] = rho * U[d]
+    F[1:1 + D] = rho * U[d] * U
+    F[1 + d] += p
+    F[D + 1] = (rho * E + p) * U[d]
+    return F
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_equilibrium_slopes_match_maxwellian_derivatives(D):
+    """a^(d) solves M0 a = dW/dx_d: on a fine grid it equals the analytic
+    derivative of ln g; A (from the compatibility condition) equals the time
+    derivative of ln g implied by the Euler equations dW/dt = -div F(W)."""
+    rng = np.random.default_rng(11)
+    vg = _fine_grid(D)
+    W = _conserved(D, 1.1, np.array([0.3, -0.2, 0.15])[:D], 1.05)
+    gradW = rng.normal(0, 0.1, size=(D, D + 2))
+    n = np.zeros(D)
+    n[0] = 1.0
+    W0, a, A = oracle.face_equilibrium(D, vg["u"], vg["w"], n, W, W, gradW)
+    for d in range(D):
+        assert np.allclose(a[d], _slope_map(D, W, gradW[d]), rtol=0, atol=1e-9)
+    eps = 1e-5
+    dWdt = np.zeros(D + 2)
+    for d in range(D):
+        dWdt -= (_euler_flux(D, W + eps * gradW[d], d) - _euler_flux(D, W - eps * gradW[d], d)) / (2 * eps)
+    assert np.allclose(A, _slope_map(D, W, dWdt), rtol=0, atol=1e-8)
+
+
+# --------------------------------------------------------------------------
+# whole steps: invariants and limits
+# --------------------------------------------------------------------------
+def _periodic_case(D, seed=5, Kn=0.05, Pr=2.0 / 3.0, nv=10, vmax=5.0):
+    if D == 2:
+        mesh = cs.periodic_tri_mesh(7, 6, 1.0, 0.9, jitter=0.25, seed=seed)
+        vg = cs.cartesian_vgrid((nv, nv), (-vmax, -vmax), (vmax, vmax))
+    else:
+        mesh = cs.box_mesh((4, 3, 3), (1.0, 0.8, 0.7), {k: "periodic" for k in ("x-", "x+", "y-", "y+", "z-", "z+")})
+        vg = cs.cartesian_vgrid((nv, nv, nv), (-vmax,) * 3, (vmax,) * 3)
+    pr = cs.params(Kn, Pr=Pr)
+    return mesh, vg, pr
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_periodic_conservation(D):
+    """Fluxes telescope: total mass, momentum and energy are conserved to
+    rounding over many steps of a far-from-equilibrium state."""
+    mesh, vg, pr = _periodic_case(D)
+    init = cs.smooth_state(mesh, seed=7, amp=0.15, U0=[0.3, -0.1, 0.05][:D])
+    o = oracle.OracleCase(mesh, vg, pr, init)
+    f, W, _ = o.state()
+    o.set_state(f * cs.perturbation(f.shape, seed=8, amp=0.2), W)
+    vol = mesh["cell_vol"]
+    tot0 = vol @ W
+    o.step(12)
+    f1, W1, _ = o.state()
+    tot1 = vol @ W1
+    scale = np.abs(tot0).max()
+    assert np.abs(tot1 - tot0).max() <= 2e-14 * scale, tot1 - tot0
+    assert np.isfinite(f1).all() and np.abs(W1 - W).max() > 1e-4   # the state did evolve
+
+
+@pytest.mark.parametrize("D,Pr,U", [(2, 1.0, [0.8, -0.5]), (2, 2.0 / 3.0, [0.0, 0.0]),
+                                    (3, 1.0, [0.4, 0.3, -0.6])])
+def test_uniform_state_is_stationary(D, Pr, U):
+    mesh, vg, pr = _periodic_case(D, Pr=Pr)
+    C = len(mesh["cell_vol"])
+    o = oracle.OracleCase(mesh, vg, pr, cs.uniform_state(C, D, 1.2, U, 0.9))
+    f0, W0, _ = o.state()
+    o.step(5)
+    f1, W1, _ = o.state()
+    assert np.abs(f1 - f0).max() <= 1e-13 * np.abs(f0).max()
+    assert np.abs(W1 - W0).max() <= 1e-13 * np.abs(W0).max()
+
+
+def test_collision_relaxation_closed_form():
+    """Spatially uniform non-equilibrium f with BGK (Pr=1): the trapezoid
+    source term split into stages 1 and 2 gives
+    f^{n+1} - g = (f^n - g)(1 - x/2)/(1 + x/2), x = dt/tau."""
+    mesh = cs.quad_mesh(3, 3, left="periodic", right="periodic", bottom="periodic", top="periodic")
+    vg = cs.cartesian_vgrid((12, 12), (-5, -5), (5, 5))
+    pr = cs.params(0.02, Pr=1.0)
+    o = oracle.OracleCase(mesh, vg, pr, cs.uniform_state(9, 2))
+    g, W, _ = o.state()
+    pert = cs.perturbation(g.shape[1:], seed=3, amp=0.3)
+    f0 = g * pert[None]
+    o.set_state(f0, W)
+    tau = o.mu_ref  # rho = T = 1: tau = mu_ref
+    x = o.dt / tau
+    r = (1 - x / 2) / (1 + x / 2)
+    o.step(4)
+    f4, W4, _ = o.state()
+    assert np.abs(W4 - W).max() < 1e-14
+    assert np.abs((f4 - g) - (f0 - g) * r ** 4).max() <= 1e-14 * np.abs(g).max()
+
+
+def test_free_molecular_limit_is_fromm_scheme():
+    """Kn -> infinity, no limiter, uniform 1-D periodic grid: the UGKS step is
+    pure second-order upwind transport with centred slopes, i.e. Fromm's
+    scheme for every discrete velocity."""
+    nx = 16
+    mesh = cs.quad_mesh(nx, 1, 1.0, 0.25, left="periodic", right="periodic",
+                        bottom="periodic", top="periodic")
+    vg = cs.cartesian_vgrid((9, 3), (-2, -1), (2, 1))
+    h = 1.0 / nx
+    pr = cs.params(float("inf"), limiter=0, dt=0.8 * h / 2.0)
+    o = oracle.OracleCase(mesh, vg, pr, cs.uniform_state(nx, 2))
+    g, W, _ = o.state()
+    rng = np.random.default_rng(4)
+    prof = 1 + 0.3 * np.sin(2 * np.pi * np.arange(nx) / nx + rng.uniform(0, 6, size=(2, 1, 1)))
+    f0 = g * prof.transpose(2, 0, 1)[:, :, :1] * rng.uniform(0.9, 1.1, size=(nx, 2, 1))
+    f0 = np.ascontiguousarray(f0)
+    o.set_state(f0, W)
+    o.step(1)
+    f1, _, _ = o.state()
+    dt = o.dt
+    ux = vg["u"][:, 0]
+    for k in range(len(ux)):
+        for c in range(2):
+            v = f0[:, c, k]
+            nu = ux[k] * dt / h
+            if nu >= 0:
+                fm1, fm2, fp1 = np.roll(v, 1), np.roll(v, 2), np.roll(v, -1)
+                ref = v - nu / 4 * (fp1 + 3 * v - 5 * fm1 + fm2) + nu * nu / 4 * (fp1 - v - fm1 + fm2)
+            else:
+                a = -nu
+                fp1, fp2, fm1 = np.roll(v, -1), np.roll(v, -2), np.roll(v, 1)
+                ref = v - a / 4 * (fm1 + 3 * v - 5 * fp1 + fp2) + a * a / 4 * (fm1 - v - fp1 + fp2)
+            assert np.abs(f1[:, c, k] - ref).max() <= 1e-14 * np.abs(v).max(), (k, c)
+
+
+def test_wall_rest_gas_is_stationary():
+    """Gas at rest at the wall temperature in a closed box: rho_w = rho and
+    nothing moves (velocity grid wide enough that truncation is < 1e-14)."""
+    mesh = cs.quad_mesh(6, 5, 1.0, 0.8, left=("wall", 0), right=("wall", 0),
+                        bottom=("wall", 0), top=("wall", 0))
+    vg = cs.cartesian_vgrid((41, 41), (-8.5, -8.5), (8.5, 8.5))
+    pr = cs.params(0.1, walls=[{"T": 1.0, "U": [0, 0, 0]}])
+    o = oracle.OracleCase(mesh, vg, pr, cs.uniform_state(30, 2))
+    f0, W0, _ = o.state()
+    o.step(4)
+    f1, W1, _ = o.state()
+    nwall = int((mesh["face_type"] == cs.WALL).sum())
+    assert np.abs(o.wall_rho(nwall) - 1.0).max() < 1e-13
+    assert np.abs(W1 - W0).max() < 1e-13
+    assert np.abs(f1 - f0).max() < 1e-13 * np.abs(f0).max()
+
+
+def test_wall_zero_penetration_and_mass_conservation():
+    """Eq. maxWalldes: no net mass flux through any wall face, so a closed
+    lid-driven cavity keeps its mass to rounding."""
+    case = cs.cavity_case(n=6, nv=12)
+    mesh = case["mesh"]
+    o = oracle.OracleCase(mesh, case["vgrid"], case["params"], case["init"])
+    vol = mesh["cell_vol"]
+    m0 = vol @ o.state()[1][:, 0]
+    for _ in range(3):
+        o.step(1)
+        Fm = o.face_macro_flux()
+        wall = mesh["face_type"] == cs.WALL
+        assert np.abs(Fm[wall, 0]).max() < 1e-16
+        assert np.abs(Fm[wall, 1:3]).max() > 1e-6      # momentum does cross (shear, pressure)
+    m1 = vol @ o.state()[1][:, 0]
+    assert abs(m1 - m0) < 1e-15
+
+
+def test_cavity_lid_drives_flow_in_its_direction():
+    case = cs.cavity_case(n=8, nv=16)
+    o = oracle.OracleCase(case["mesh"], case["vgrid"], case["params"], case["init"])
+    o.step(30)
+    _, W, _ = o.state()
+    x = case["mesh"]["cell_xc"]
+    U = W[:, 1] / W[:, 0]
+    top = x[:, 1] > 0.9
+    bottom = x[:, 1] < 0.1
+    assert U[top].mean() > 0.01 and U[bottom].mean() < U[top].mean()
+
+
+def test_free_molecular_wall_outflow_translates_linear_data():
+    """Kn -> infinity, no limiter: for velocities leaving through the right
+    wall (u_x > 0) every cell, including the one next to that wall, moves a
+    linear profile exactly along the characteristics, f(x - u dt).  This fixes
+    the sign of the wall's free-transport term (f_in - t u.grad f_in)."""
+    nx = 10
+    mesh = cs.quad_mesh(nx, 1, 1.0, 0.1, left=("wall", 0), right=("wall", 0),
+                        bottom="periodic", top="periodic")
+    vg = cs.cartesian_vgrid((7, 3), (-2, -1), (2, 1))
+    h = 1.0 / nx
+    pr = cs.params(float("inf"), limiter=0, dt=0.7 * h / 2.0, walls=[{"T": 1.0, "U": [0, 0, 0]}])
+    o = oracle.OracleCase(mesh, vg, pr, cs.uniform_state(nx, 2))
+    g, W, _ = o.state()
+    x = mesh["cell_xc"][:, 0]
+    beta = np.array([0.3, -0.2])
+    f0 = g * (1.0 + beta[None, :, None] * x[:, None, None])
+    o.set_state(f0, W)
+    o.step(1)
+    f1, _, _ = o.state()
+    ux = vg["u"][:, 0]
+    for k in np.nonzero(ux > 0)[0]:
+        shift = ux[k] * o.dt
+        ref = g[:, :, k] * (1.0 + beta[None, :] * (x[:, None] - shift))
+        assert np.abs(f1[1:, :, k] - ref[1:]).max() <= 1e-14 * np.abs(g).max(), k
+
+
+def test_macro_update_is_moment_of_micro_update_free_molecular():
+    """With no collisions (Kn -> infinity) the W update of Eq. macroscopicUpdata
+    and the f update carry the same fluxes, so W^{n+1} - W^n equals the
+    discrete moments sum_k w_k psi_k (f^{n+1} - f^n), with walls and far field."""
+    case = cs.cylinder_case(n_cells=900, nvx=14, nvy=12, mach=2.0)
+    pr = dict(case["params"])
+    pr["Kn"] = float("inf")
+    mesh = case["mesh"]
+    o = oracle.OracleCase(mesh, case["vgrid"], pr, cs.smooth_state(mesh, 3, 0.1, U0=[0.5, 0.2]))
+    f0, W0, _ = o.state()
+    f0 = f0 * cs.perturbation(f0.shape, 9, 0.15)
+    o.set_state(f0, W0)
+    o.step(1)
+    f1, W1, _ = o.state()
+    u, w = case["vgrid"]["u"], case["vgrid"]["w"]
+    df = f1 - f0
+    dW = np.stack([df[:, 0] @ w, df[:, 0] @ (w * u[:, 0]), df[:, 0] @ (w * u[:, 1]),
+                   0.5 * (df[:, 0] @ (w * (u * u).sum(1)) + df[:, 1] @ w)], 1)
+    assert np.abs((W1 - W0) - dW).max() <= 1e-13 * np.abs(W0).max()
+
+
+def test_limited_reconstruction_stays_within_neighbour_bounds():
+    """Venkatakrishnan with eps -> 0: every face value f_i + phi grad f_i . r
+    lies between the minimum and maximum over cell i and its neighbours."""
+    case = cs.cylinder_case(n_cells=1200, nvx=4, nvy=4)
+    mesh = case["mesh"]
+    pr = dict(case["params"])
+    pr["venkat_K"] = 1e-7
+    o = oracle.OracleCase(mesh, case["vgrid"], pr, case["init"])
+    rng = np.random.default_rng(2)
+    x = mesh["cell_xc"]
+    phi = np.sin(1.3 * x[:, 0]) * np.cos(0.7 * x[:, 1]) + 0.3 * rng.normal(size=len(x))
+    ghost_pts = _ghost_points(mesh)
+    ghost = np.sin(1.3 * ghost_pts[:, 0]) * np.cos(0.7 * ghost_pts[:, 1])
+    g = o.scalar_gradient(phi, ghost, limited=True)
+    gu = o.scalar_gradient(phi, ghost, limited=False)
+    fc, ft = mesh["face_cells"], mesh["face_type"]
+    lo, hi = phi.copy(), phi.copy()
+    for f in range(len(ft)):
+        i, j = fc[f]
+        if ft[f] == cs.FARFIELD:
+            lo[i] = min(lo[i], ghost[f]); hi[i] = max(hi[i], ghost[f])
+        elif ft[f] in (cs.INTERIOR, cs.PERIODIC):
+            lo[i] = min(lo[i], phi[j]); hi[i] = max(hi[i], phi[j])
+            lo[j] = min(lo[j], phi[i]); hi[j] = max(hi[j], phi[i])
+    for f in range(len(ft)):
+        for s in (0, 1):
+            i = fc[f, s]
+            if i < 0:
+                continue
+            v = phi[i] + g[i] @ (mesh["face_xc"][f] - mesh["face_shift"][f] * s - x[i])
+            assert lo[i] - 1e-9 <= v <= hi[i] + 1e-9
+    assert np.abs(g - gu).max() > 0.1       # the limiter did act somewhere
+
+
+def test_continuum_limit_navier_stokes_fluxes():
+    """Small Kn: the interface flux of a smooth shear / temperature gradient is
+    the Navier-Stokes one, shear stress mu dU/dy and heat flux
+    -(5/2) mu/Pr dT/dy (monatomic gas, Shakhov Prandtl number)."""
+    ny = 20
+    mesh = cs.quad_mesh(1, ny, 0.05, 1.0, left="periodic", right="periodic",
+                        bottom=("wall", 0), top=("wall", 1))
+    vg = cs.cartesian_vgrid((32, 32), (-6, -6), (6, 6))
+    Uw, dTw = 0.02, 0.02
+    pr = cs.params(5e-4, Pr=2.0 / 3.0, omega=0.81,
+                   walls=[{"T": 1 - dTw, "U": [-Uw, 0, 0]}, {"T": 1 + dTw, "U": [Uw, 0, 0]}])
+    y = mesh["cell_xc"][:, 1]
+    init = cs.uniform_state(ny, 2)
+    init[:, 1] = Uw * (2 * y - 1)
+    init[:, 3] = 1 + dTw * (2 * y - 1)
+    init[:, 0] = 1.0 / init[:, 3]       # uniform pressure: no acoustic transient
+    o = oracle.OracleCase(mesh, vg, pr, init)
+    assert o.dt / o.mu_ref > 5          # collision-dominated
+    # the trapezoid factor (1 - x/2)/(1 + x/2) ~ -0.64 per step: 20 steps relax
+    # the non-equilibrium part to its Chapman-Enskog value; the linear profiles
+    # stay put (diffusion length sqrt(nu t) ~ 0.007)
+    o.step(20)
+    Fm = o.face_macro_flux()
+    fy = np.nonzero((mesh["face_n"][:, 1] > 0.5) & (np.abs(mesh["face_xc"][:, 1] - 0.5) < 1e-9))[0][0]
+    mu = o.mu_ref                       # T = 1 at mid-channel
+    shear = -Fm[fy, 1] / o.dt           # momentum flux = -tau_xy
+    heat = Fm[fy, 3] / o.dt
+    assert abs(shear / (mu * 2 * Uw) - 1) < 0.03, shear / (mu * 2 * Uw)
+    kappa = 2.5 * mu / pr["Pr"]
+    assert abs(heat / (-kappa * 2 * dTw) - 1) < 0.03, heat / (-kappa * 2 * dTw)
+    qcell = o.state()[2][ny // 2 - 1: ny // 2 + 1, 1].mean()
+    assert abs(qcell / (-kappa * 2 * dTw) - 1) < 0.03, qcell / (-kappa * 2 * dTw)
