@@ -88,6 +88,7 @@ def lib():
                                           D_P, D_P, D_P]
         L.or_moment_matrix.argtypes = [ct.c_int32, ct.c_int64, D_P, D_P, D_P, D_P]
         L.or_scalar_gradient.argtypes = [ct.c_void_p, D_P, D_P, ct.c_int32, D_P]
+        L.or_micro_gradient.argtypes = [ct.c_void_p, D_P, D_P, D_P, D_P]
         L.or_mu_ref.restype = ct.c_double
         L.or_mu_ref.argtypes = [ct.c_void_p]
         _lib = L
@@ -178,6 +179,13 @@ class OracleCase:
         F = np.empty((self.F, self.D + 2))
         lib().or_face_macro_flux(self._h, _p(F))
         return F
+
+    def micro_gradient(self, phi, u, phi_ghost=None):
+        phi, u = _c(phi), _c(u)
+        g = _c(phi_ghost) if phi_ghost is not None else None
+        out = np.empty((self.C, self.D))
+        lib().or_micro_gradient(self._h, _p(phi), _p(g), _p(u), _p(out))
+        return out
 
     def scalar_gradient(self, phi, phi_ghost=None, limited=False):
         phi = _c(phi)

@@ -511,14 +511,18 @@ or_case *or_create(const or_mesh *m, const or_vgrid *v, const or_params *p,
         /* READING: h_i = 2 D |Omega_i| / sum_f S_f (edge length of a square or
          * cube, twice the inradius of a simplex); Venkatakrishnan eps^2 = (K h)^3 */
         double hi = 2.0 * D * c->cell_vol[i] / sumS;
-        if (hi < hmin) hmin = hi;
+        double hcfl = 2.0 * c->cell_vol[i] / sumS;
+        if (hcfl < hmin) hmin = hcfl;
         double Kh = p->venkat_K * hi;
         c->eps2[i] = Kh * Kh * Kh;
     }
     free(dvec);
 
-    /* READING (Alg. 1 line 1): dt = CFL min_i h_i / max_k |u_k|, fixed for a
-     * fixed velocity grid */
+    /* READING (Alg. 1 line 1): the CFL condition of the upwind finite-volume
+     * update, dt <= |Omega_i| / sum_f S_f (u_k . n_f)^+; since the positive
+     * part is at most |u_k| sum_f S_f / 2, dt = CFL min_i (2 |Omega_i| /
+     * sum_f S_f) / max_k |u_k| (= CFL h_i / (D max|u|)), fixed for a fixed
+     * velocity grid */
     double umax = 0.0;
     for (int64_t k = 0; k < Nv; ++k) {
         double s = 0.0;
@@ -643,6 +647,50 @@ static void lsq_gradient(const or_case *c, int64_t i, const double *val, int64_t
         if (ph < phi) phi = ph;
     }
     for (int d = 0; d < D; ++d) g[d] *= phi;
+}
+
+/* Micro reconstruction of f_k at cell i (Sec. 3.1 Step 2): the limited
+ * least-squares slope, then scaled by theta in [0, 1] so that the linear
+ * reconstruction is non-negative wherever the step evaluates it.
+ * READING: f is a density; the free-transport part of the flux is a
+ * positively weighted time average of f_i + grad f . (x_f - x_i - t u_k),
+ * 0 <= t <= dt, so the reconstruction is required to be >= 0 at every face
+ * centre (t = 0) and at the foot of the characteristic (t = dt).  If the
+ * smallest of these values v is negative, theta = f_i / (f_i - v) (0 if
+ * f_i <= 0); otherwise theta = 1 (a positivity-preserving scaling in the
+ * manner of Zhang and Shu).  Venkatakrishnan's eps^2 = (K h)^3 is
+ * dimensional and leaves small f (velocity tails, near-vacuum wakes)
+ * unlimited, which is where the scaling acts. */
+static void micro_gradient(const or_case *c, int64_t i, const double *val, int64_t stride,
+                           const double *gval, int64_t gstride, const double *uk, double *g)
+{
+    int D = c->D;
+    lsq_gradient(c, i, val, stride, gval, gstride, c->p.limiter, g);
+    double vi = val[i * stride];
+    double vmin = vi;
+    for (int64_t s = c->cf_ptr[i]; s < c->cf_ptr[i + 1]; ++s) {
+        double v0 = vi, v1 = vi;
+        for (int d = 0; d < D; ++d) {
+            v0 += g[d] * c->cf_r[s * D + d];
+            v1 += g[d] * (c->cf_r[s * D + d] - c->dt * uk[d]);
+        }
+        if (v0 < vmin) vmin = v0;
+        if (v1 < vmin) vmin = v1;
+    }
+    if (vmin < 0.0) {
+        double theta = vi > 0.0 ? vi / (vi - vmin) : 0.0;
+        for (int d = 0; d < D; ++d) g[d] *= theta;
+    }
+}
+
+void or_micro_gradient(or_case *c, const double *phi, const double *phi_ghost, const double *uk,
+                       double *grad)
+{
+    double *gv = (double *)malloc(sizeof(double) * (c->F ? c->F : 1));
+    for (int64_t f = 0; f < c->F; ++f)
+        gv[f] = phi_ghost ? phi_ghost[f] : phi[c->face_cells[2 * f]];
+    for (int64_t i = 0; i < c->C; ++i) micro_gradient(c, i, phi, 1, gv, 1, uk, grad + i * c->D);
+    free(gv);
 }
 
 void or_scalar_gradient(or_case *c, const double *phi, const double *phi_ghost, int32_t limited,
@@ -789,12 +837,12 @@ static void one_step(or_case *c)
             if (nc == 2) c->ghost_k[f * nc + 1] = B;
         }
 
-        /* line 5: reconstruct f_k (limited least-squares slope per component) */
+        /* line 5: reconstruct f_k (limited, positivity-scaled slope per component) */
 #pragma omp parallel for num_threads(nt) schedule(static)
         for (int64_t i = 0; i < C; ++i)
             for (int cc = 0; cc < nc; ++cc)
-                lsq_gradient(c, i, c->f + cc * Nv + k, (int64_t)nc * Nv, c->ghost_k + cc, nc,
-                             c->p.limiter, c->grad_k + (i * nc + cc) * D);
+                micro_gradient(c, i, c->f + cc * Nv + k, (int64_t)nc * Nv, c->ghost_k + cc, nc, uk,
+                               c->grad_k + (i * nc + cc) * D);
 
         /* line 6: flux F_k through every non-wall face (Eq. microscopicFlux,
          * Eq. fullSolution) and its macroscopic contribution (Eq. macroscopicFlux) */

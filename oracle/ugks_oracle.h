@@ -99,6 +99,10 @@ void or_moment_matrix(int32_t D, int64_t nv, const double *u, const double *w,
  * values per face (far-field faces only; NULL -> owner value) */
 void or_scalar_gradient(or_case *c, const double *phi, const double *phi_ghost,
                         int32_t limited, double *grad);
+/* micro reconstruction of a scalar field at velocity u (limited least-squares
+ * slope with the positivity scaling of the oracle's step) */
+void or_micro_gradient(or_case *c, const double *phi, const double *phi_ghost, const double *uk,
+                       double *grad);
 /* mu_ref and tau of the VHS viscosity law used by the case */
 double or_mu_ref(const or_case *c);
 
