@@ -1,0 +1,301 @@
+"""Benchmark of the UGKS hot path on GB300: cell-velocity updates per second.
+
+Default workload: the 2D Mach-5 argon cylinder at Kn 0.1 (seeded Delaunay
+mesh of ~30,000 triangles, 60x50 Cartesian velocity grid), FP32-storage /
+FP64-moment form; the plain FP64 path is timed beside it.  One step = one full
+UGKS time step (all kernels of Algorithm 1) of the whole case.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ugks|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs one independent replica per GPU
+(the method needs no exchange between independent cases): value = all cells x
+velocities updated by all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-velocity updates/s"
+UNIT = "cvu/s"
+WORKLOAD = "cylinder_Ma5_Kn0.1_tri30k_v60x50"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        pw = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def _workload(name):
+    from paper_2412_06546_gb300 import cases
+    if name == WORKLOAD:
+        return cases.cylinder_case(n_cells=30000, nvx=60, nvy=50, mach=5.0, Kn=0.1, seed=2)
+    if name == "cavity20_v24":
+        return cases.cavity_case()
+    if name == "sphere_Ma4_Kn0.1_tet150k_v28":
+        return cases.sphere_case()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _time_steps(torch, g, steps, warmup, dist, sampler_index, profile=True):
+    g.step(warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if profile:
+        g.profile_begin(steps)
+    st = torch.cuda.ExternalStream(g.stream) if g.stream else torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(sampler_index) as cs:
+        e0.record(st)
+        g.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    groups, n = g.profile_end() if profile else ({}, 0)
+    return ms, groups, cs.summary()
+
+
+def _max_over_ranks(torch, dist, v):
+    if not dist:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _cpu_baseline(case, steps=1):
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    o = oracle.OracleCase(case["mesh"], case["vgrid"], case["params"], case["init"], n_threads=cores)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    C, Nv = o.C, o.Nv
+    return {"value": C * Nv * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full step(s) of the same case on the host cores (OpenMP), {dt:.1f} s"}
+
+
+def run_reference(args):
+    dist_rank = int(os.environ.get("RANK", "0"))
+    if dist_rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    case = _workload(args.workload)
+    cores = os.cpu_count() or 1
+    o = oracle.OracleCase(case["mesh"], case["vgrid"], case["params"], case["init"], n_threads=cores)
+    o.step(args.ref_warmup)
+    times = []
+    for _ in range(args.ref_steps):
+        t0 = time.perf_counter()
+        o.step(1)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = o.C * o.Nv / (ms * 1e-3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.ref_steps, "warmup": args.ref_warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "cells": o.C, "nv": o.Nv, "form": "fp64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.ref_steps} full steps of the same case after {args.ref_warmup} warm-up"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ugks", choices=["ugks", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fp64-steps", type=int, default=0, help="steps of the FP64 plain path (0: steps/10)")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--ref-steps", type=int, default=0)
+    ap.add_argument("--ref-warmup", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--patch", type=int, default=0)
+    ap.add_argument("--vtile", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        args.ref_steps = args.ref_steps or args.steps
+        args.ref_warmup = args.ref_warmup if args.ref_warmup else args.warmup
+        # each oracle step is a full step of the case; bound the run to a few minutes
+        args.ref_steps = min(args.ref_steps, 5)
+        args.ref_warmup = min(args.ref_warmup, 1)
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU (no CPU fallback)")
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2412_06546_gb300 import build, _lib
+    build.build()
+    case = _workload(args.workload)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32,
+                      stream=stream.cuda_stream, patch_cells=args.patch, vtile=args.vtile)
+    info = g.info()
+    C, Nv, nc = info["n_cells"], info["nv"], info["ncomp"]
+    ms, groups, clocks = _time_steps(torch, g, args.steps, args.warmup, dist, local)
+    g.check()
+    ms = _max_over_ranks(torch, dist, ms)
+    ms_step = ms / args.steps
+    value = ws * C * Nv / (ms_step * 1e-3)
+    launches = info["kernel_launches_per_step"] * args.steps
+
+    # roofline of the dominant kernel (gather pass): 1 read + 1 write of f
+    peak, peak_kind = _peaks()
+    g_ms = groups.get("gather", 0.0) / max(args.steps, 1)
+    alg_bytes = 2 * C * nc * Nv * 4
+    achieved = alg_bytes / (g_ms * 1e-3) / 1e9 if g_ms > 0 else None
+    share = {k: round(v / max(sum(groups.values()), 1e-12), 4) for k, v in groups.items()}
+
+    # e2e: state in pinned host memory -> ugks_set_state -> ugks_step -> ugks_moments
+    f_h, W_h = g.state()
+    f_pin = torch.from_numpy(f_h).pin_memory().numpy()
+    W_pin = torch.from_numpy(W_h).pin_memory().numpy()
+    g.set_state(f_pin, W_pin)
+    g.step(1)
+    g.moments()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        g.set_state(f_pin, W_pin)
+        g.step(1)
+        g.moments()
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(torch, dist, time.perf_counter() - t0) / args.e2e_steps
+    e2e = {"value": ws * C * Nv / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(f_pin.nbytes + W_pin.nbytes),
+           "d2h_bytes_per_step": int(C * (2 * info["dim"] + 2) * 8)}
+    g.close()
+
+    # the plain FP64 path on the same case
+    fp64_steps = args.fp64_steps or max(3, args.steps // 10)
+    with torch.cuda.stream(stream):
+        g64 = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP64,
+                        stream=stream.cuda_stream)
+    ms64, groups64, _ = _time_steps(torch, g64, fp64_steps, 2, dist, local)
+    g64.check()
+    ms64 = _max_over_ranks(torch, dist, ms64) / fp64_steps
+    v64 = ws * C * Nv / (ms64 * 1e-3)
+    g64.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(case)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": C, "nv": Nv, "faces": info["n_faces"],
+                   "form": "fp32 storage, fp64 moments", "patch_cells": info["patch_cells"],
+                   "vtile": info["vtile"], "l2": f"inputs larger than L2 (f {info['f_bytes'] / 1e9:.2f} GB per copy)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "kernel": "k_gather", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
+                     "launch_ms": g_ms, "group_share": share},
+        "fp64_plain": {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": fp64_steps,
+                       "speedup_of_fp32_form": value / v64},
+        "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+        "step_hbm_frac_1R1W": value / ws * 4 * nc * 2 / (peak * 1e9),
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

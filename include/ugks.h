@@ -1,0 +1,182 @@
+/*
+ * ugks.h -- C ABI of the GB300 unified gas-kinetic scheme (UGKS) library.
+ *
+ * One explicit UGKS time step on an unstructured physical mesh times a
+ * discrete velocity space, as defined in Zhang, Wei, Long, Xu, "An efficiency
+ * and memory-saving programming paradigm for the unified gas-kinetic scheme"
+ * (arXiv:2412.06546): BGK-Shakhov model with reduced distributions h, b
+ * (Sec. 2.1-2.2), finite-volume update of f and W (Sec. 2.3, Eq.
+ * microscopicFlux, macroscopicUpdata, macroscopicFlux), the time-integrated
+ * interface solution (Sec. 2.4, Eq. fullSolution), ghost far field and Maxwell
+ * isothermal walls (Sec. 2.5, Eq. maxWalldes), the trapezoid source term
+ * (Sec. 2.6) and the two-stage update of Algorithm 1 (Sec. 3.2, Eq. microS1,
+ * microS2).  Every step of the path runs in the library's CUDA kernels.
+ *
+ * Units: gas constant R = 1, reference density and temperature 1, velocities
+ * in sqrt(R T_ref).  Monatomic gas (argon, K = 0 internal degrees of freedom):
+ * 2D cases store h and b per velocity, 3D cases store h only (b = 0).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a ugks_status; no exception or abort crosses the ABI.
+ *    On failure ugks_last_error() returns a thread-local message.
+ *  - Input arrays are host pointers, copied by the call; the caller keeps
+ *    ownership.  Output arrays are caller-owned host buffers unless the name
+ *    says "device".
+ *  - A case handle is used from one host thread at a time.
+ *  - Device memory comes from the ugks_alloc callbacks (NULL: cudaMalloc /
+ *    cudaFree) and work is issued on the stream given at creation.
+ */
+#ifndef UGKS_H
+#define UGKS_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    UGKS_OK = 0,
+    UGKS_EINVAL = 1,        /* invalid argument (message says which) */
+    UGKS_ENOMEM = 2,        /* device or host allocation failed */
+    UGKS_ECUDA = 3,         /* a CUDA runtime call failed */
+    UGKS_ENUMERIC = 4,      /* non-finite or non-positive density/temperature */
+    UGKS_ENOTCONVERGED = 5, /* a served case hit its step limit */
+    UGKS_EBUSY = 6,         /* server cannot admit the request now */
+    UGKS_ETIMEOUT = 7,      /* bounded wait ran out */
+    UGKS_ENOTFOUND = 8      /* unknown ticket */
+} ugks_status;
+
+/* face types (Sec. 2.5; PERIODIC is an addition for closed test domains) */
+enum { UGKS_FACE_INTERIOR = 0, UGKS_FACE_WALL = 1, UGKS_FACE_FARFIELD = 2, UGKS_FACE_PERIODIC = 3 };
+
+/* precision of the stored distribution and the per-velocity arithmetic.
+ * UGKS_FP64: everything in FP64 (the plain method).
+ * UGKS_FP32: f stored and streamed in FP32, per-velocity arithmetic in FP32,
+ * velocity-moment sums promoted to FP64 per tile, and FP64 for W, the
+ * equilibrium parameters, the heat flux and the collision coefficients. */
+enum { UGKS_FP64 = 0, UGKS_FP32 = 1 };
+
+/* Unstructured physical mesh (Sec. 2.3): cells Omega_i and faces S_ij. */
+typedef struct {
+    int32_t dim;              /* 2 or 3 */
+    int64_t n_cells, n_faces;
+    const double *cell_xc;    /* [n_cells][dim] centroids */
+    const double *cell_vol;   /* [n_cells] |Omega_i| > 0 */
+    const int64_t *face_cells;/* [n_faces][2] owner, neighbour; -1 on wall / far field */
+    const double *face_n;     /* [n_faces][dim] unit normal, owner -> neighbour (outward at boundaries) */
+    const double *face_S;     /* [n_faces] face area S_ij > 0 */
+    const double *face_xc;    /* [n_faces][dim] face centre, as seen from the owner */
+    const int32_t *face_type; /* [n_faces] UGKS_FACE_* */
+    const int32_t *face_tag;  /* [n_faces] wall index (0 <= tag < n_walls) for WALL faces */
+    const double *face_shift; /* [n_faces][dim] or NULL: PERIODIC faces, vector added to the
+                                 neighbour centroid to bring its image next to the owner */
+} ugks_mesh;
+
+/* Discrete velocity space (Sec. 2.3): int Q du = sum_k Q_k V_k */
+typedef struct {
+    int32_t dim;
+    int64_t nv;
+    const double *u;          /* [nv][dim] velocities u_k */
+    const double *w;          /* [nv] cell volumes V_k (quadrature weights) */
+    int32_t cart_n[3];        /* > 0 for a tensor grid (informational) */
+} ugks_vgrid;
+
+/* Gas, boundary and numerical parameters */
+typedef struct {
+    double Kn;        /* Knudsen number (mean free path / L_ref); +inf: collisionless */
+    double L_ref;     /* reference length of Kn (e.g. the cylinder diameter) */
+    double Pr;        /* Prandtl number of the Shakhov model (1: BGK) */
+    double omega;     /* viscosity exponent, mu = mu_ref T^omega */
+    double cfl;       /* dt = cfl * min_i h_i / max_k |u_k| unless dt > 0 */
+    double dt;        /* fixed time step if > 0 */
+    int32_t limiter;  /* 1: Venkatakrishnan limiter on micro and macro slopes */
+    double venkat_K;  /* limiter constant K, eps^2 = (K h_i)^3 */
+    int32_t n_walls;
+    const double *wall_T;   /* [n_walls] wall temperature */
+    const double *wall_U;   /* [n_walls][3] wall velocity */
+    double inf_rho, inf_U[3], inf_T; /* far-field state */
+    int32_t precision;      /* UGKS_FP64 or UGKS_FP32 */
+    const double *prim_init;/* [n_cells][dim+2] initial (rho, U, T), or NULL: far-field state */
+    int32_t patch_cells;    /* gather tiling: cells per patch (0: automatic) */
+    int32_t vtile;          /* gather tiling: velocities per tile, 32, 64 or 128 (0: automatic) */
+} ugks_params;
+
+/* Device allocator.  alloc returns a device pointer of at least `bytes`
+ * (256-byte aligned) usable on `stream`, or NULL; free releases it. */
+typedef struct {
+    void *ctx;
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, size_t bytes, void *stream);
+} ugks_alloc;
+
+typedef struct ugks_case ugks_case;
+
+typedef struct {
+    int32_t dim, ncomp, precision;
+    int64_t n_cells, n_faces, nv, nv_pad;
+    double dt;
+    int64_t step;              /* steps taken so far */
+    size_t device_bytes;       /* device memory held by the case */
+    size_t f_bytes;            /* bytes of one copy of f */
+    int32_t n_patches, patch_cells, vtile;  /* gather tiling in use */
+    int64_t kernel_launches_per_step;
+} ugks_info_t;
+
+/* Create a case: validates and copies the inputs, orders cells for locality,
+ * builds least-squares coefficients and gather patches, allocates device state
+ * and initialises f^0 = Maxwellian(W^0) (Sec. 3.1).  `stream` is a cudaStream_t
+ * (NULL: the legacy default stream).  On success *out owns the device memory. */
+ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ugks_params *params,
+                        const ugks_alloc *alloc, void *stream, ugks_case **out);
+
+/* Advance `nsteps` time steps (Algorithm 1 each).  Asynchronous on the case
+ * stream; errors of the launches are reported, numeric checks are not (see
+ * ugks_check). */
+ugks_status ugks_step(ugks_case *c, int32_t nsteps);
+
+/* Wait for the case stream and report UGKS_ENUMERIC if the state holds a
+ * non-finite value or a non-positive density or temperature. */
+ugks_status ugks_check(ugks_case *c);
+
+/* Macroscopic fields of the current state into host buffers (any may be NULL):
+ * rho[C], U[C][dim], T[C], q[C][dim] (heat flux of f, Sec. 2.1).  Cell order is
+ * the caller's mesh order.  Synchronises the case stream. */
+ugks_status ugks_moments(ugks_case *c, double *rho, double *U, double *T, double *q);
+
+/* Residual of the last step, res[m] = |W^{n+1}_m - W^n_m|_2 / |W^n_m|_2, m < dim+2. */
+ugks_status ugks_residual(ugks_case *c, double *res);
+
+/* Copy the state to host buffers: f[C][ncomp][nv] (FP64, caller cell order) and
+ * W[C][dim+2] (conserved variables); either may be NULL.  Synchronises. */
+ugks_status ugks_get_state(ugks_case *c, double *f, double *W);
+
+/* Replace the state from host buffers (same layout); either may be NULL.
+ * The heat flux is recomputed from the new f.  Asynchronous with respect to
+ * the host after the upload is issued. */
+ugks_status ugks_set_state(ugks_case *c, const double *f, const double *W);
+
+/* Kernel-group timing.  After ugks_profile_begin(c, max_steps) the next
+ * max_steps calls of ugks_step record CUDA events on the case stream around
+ * each kernel group (no host synchronisation); ugks_profile_end synchronises
+ * and writes the summed milliseconds per group into ms[0..n-1] (groups in
+ * launch order: 0 cell prep + macro slopes, 1 face equilibrium pass,
+ * 2 wall density pass, 3 gather pass (slopes, fluxes, stage 1), 4 W update,
+ * 5 collision (stage 2) + heat flux) and the number of profiled steps into
+ * *steps.  Not part of the method; used by the benchmark. */
+ugks_status ugks_profile_begin(ugks_case *c, int32_t max_steps);
+ugks_status ugks_profile_end(ugks_case *c, double *ms, int32_t n, int32_t *steps);
+
+/* Sizes and tiling of a case. */
+ugks_status ugks_info(const ugks_case *c, ugks_info_t *info);
+
+/* Release the device memory of a case (NULL is ignored). */
+void ugks_destroy(ugks_case *c);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ugks_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UGKS_H */

@@ -1,0 +1,254 @@
+"""ctypes binding of the C ABI in ``include/ugks.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_build/libugks.so``; this
+module converts numpy arrays to the ABI structs, hands the library torch's
+caching allocator and current stream, and turns status codes into exceptions.
+There is no CPU fallback: if the library or a GPU is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libugks.so")
+
+D_P = ct.POINTER(ct.c_double)
+I64_P = ct.POINTER(ct.c_int64)
+I32_P = ct.POINTER(ct.c_int32)
+
+FP64, FP32 = 0, 1
+STATUS = {0: "UGKS_OK", 1: "UGKS_EINVAL", 2: "UGKS_ENOMEM", 3: "UGKS_ECUDA", 4: "UGKS_ENUMERIC",
+          5: "UGKS_ENOTCONVERGED", 6: "UGKS_EBUSY", 7: "UGKS_ETIMEOUT", 8: "UGKS_ENOTFOUND"}
+
+
+class UGKSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Mesh(ct.Structure):
+    _fields_ = [("dim", ct.c_int32), ("n_cells", ct.c_int64), ("n_faces", ct.c_int64),
+                ("cell_xc", D_P), ("cell_vol", D_P), ("face_cells", I64_P), ("face_n", D_P),
+                ("face_S", D_P), ("face_xc", D_P), ("face_type", I32_P), ("face_tag", I32_P),
+                ("face_shift", D_P)]
+
+
+class VGrid(ct.Structure):
+    _fields_ = [("dim", ct.c_int32), ("nv", ct.c_int64), ("u", D_P), ("w", D_P),
+                ("cart_n", ct.c_int32 * 3)]
+
+
+class Params(ct.Structure):
+    _fields_ = [("Kn", ct.c_double), ("L_ref", ct.c_double), ("Pr", ct.c_double),
+                ("omega", ct.c_double), ("cfl", ct.c_double), ("dt", ct.c_double),
+                ("limiter", ct.c_int32), ("venkat_K", ct.c_double), ("n_walls", ct.c_int32),
+                ("wall_T", D_P), ("wall_U", D_P), ("inf_rho", ct.c_double),
+                ("inf_U", ct.c_double * 3), ("inf_T", ct.c_double), ("precision", ct.c_int32),
+                ("prim_init", D_P), ("patch_cells", ct.c_int32), ("vtile", ct.c_int32)]
+
+
+ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p)
+FREE_FN = ct.CFUNCTYPE(None, ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p)
+
+
+class Alloc(ct.Structure):
+    _fields_ = [("ctx", ct.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN)]
+
+
+class Info(ct.Structure):
+    _fields_ = [("dim", ct.c_int32), ("ncomp", ct.c_int32), ("precision", ct.c_int32),
+                ("n_cells", ct.c_int64), ("n_faces", ct.c_int64), ("nv", ct.c_int64),
+                ("nv_pad", ct.c_int64), ("dt", ct.c_double), ("step", ct.c_int64),
+                ("device_bytes", ct.c_size_t), ("f_bytes", ct.c_size_t), ("n_patches", ct.c_int32),
+                ("patch_cells", ct.c_int32), ("vtile", ct.c_int32),
+                ("kernel_launches_per_step", ct.c_int64)]
+
+
+EXPORTS = {
+    "ugks_create": (ct.c_int, [ct.POINTER(Mesh), ct.POINTER(VGrid), ct.POINTER(Params), ct.POINTER(Alloc),
+                               ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    "ugks_step": (ct.c_int, [ct.c_void_p, ct.c_int32]),
+    "ugks_check": (ct.c_int, [ct.c_void_p]),
+    "ugks_moments": (ct.c_int, [ct.c_void_p, D_P, D_P, D_P, D_P]),
+    "ugks_residual": (ct.c_int, [ct.c_void_p, D_P]),
+    "ugks_get_state": (ct.c_int, [ct.c_void_p, D_P, D_P]),
+    "ugks_set_state": (ct.c_int, [ct.c_void_p, D_P, D_P]),
+    "ugks_info": (ct.c_int, [ct.c_void_p, ct.POINTER(Info)]),
+    "ugks_profile_begin": (ct.c_int, [ct.c_void_p, ct.c_int32]),
+    "ugks_profile_end": (ct.c_int, [ct.c_void_p, D_P, ct.c_int32, ct.POINTER(ct.c_int32)]),
+    "ugks_destroy": (None, [ct.c_void_p]),
+    "ugks_last_error": (ct.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+        L = ct.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code):
+    if code != 0:
+        raise UGKSError(code, load().ugks_last_error().decode())
+
+
+def _c(a, dt=np.float64):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _p(a, typ=D_P):
+    return a.ctypes.data_as(typ) if a is not None else None
+
+
+def make_structs(mesh, vgrid, params, init=None, precision=FP64, patch_cells=0, vtile=0):
+    """Marshal the dicts of ``cases`` into ABI structs; returns (structs, keepalive)."""
+    keep = []
+    D = int(mesh["dim"])
+    arr = {k: _c(mesh[k]) for k in ("cell_xc", "cell_vol", "face_n", "face_S", "face_xc", "face_shift")}
+    arr["face_cells"] = _c(mesh["face_cells"], np.int64)
+    arr["face_type"] = _c(mesh["face_type"], np.int32)
+    arr["face_tag"] = _c(mesh["face_tag"], np.int32)
+    keep.append(arr)
+    m = Mesh(D, len(arr["cell_vol"]), len(arr["face_S"]), _p(arr["cell_xc"]), _p(arr["cell_vol"]),
+             _p(arr["face_cells"], I64_P), _p(arr["face_n"]), _p(arr["face_S"]), _p(arr["face_xc"]),
+             _p(arr["face_type"], I32_P), _p(arr["face_tag"], I32_P), _p(arr["face_shift"]))
+    u, w = _c(vgrid["u"]), _c(vgrid["w"])
+    keep += [u, w]
+    cart = list(vgrid.get("cart_n", [0, 0, 0])) + [0, 0, 0]
+    v = VGrid(D, len(w), _p(u), _p(w), (ct.c_int32 * 3)(*cart[:3]))
+    walls = params.get("walls") or []
+    wT = _c([wl["T"] for wl in walls] or [1.0])
+    wU = _c([list(wl["U"]) + [0.0] * (3 - len(wl["U"])) for wl in walls] or [[0.0, 0.0, 0.0]])
+    keep += [wT, wU]
+    inf = params.get("inf") or {"rho": 1.0, "U": [0.0, 0.0, 0.0], "T": 1.0}
+    iU = list(inf["U"]) + [0.0] * (3 - len(inf["U"]))
+    ini = _c(init) if init is not None else None
+    keep.append(ini)
+    p = Params(params["Kn"], params.get("L_ref", 1.0), params["Pr"], params["omega"], params["cfl"],
+               params.get("dt", 0.0), params.get("limiter", 1), params.get("venkat_K", 1.0), len(walls),
+               _p(wT), _p(wU), inf["rho"], (ct.c_double * 3)(*iU), inf["T"], int(precision), _p(ini),
+               int(patch_cells), int(vtile))
+    return (m, v, p), keep
+
+
+class _TorchAllocator:
+    """torch's caching allocator behind the ugks_alloc callbacks."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.live = {}
+
+        def _alloc(ctx, nbytes, stream):
+            ptr = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream or 0)
+            self.live[ptr] = nbytes
+            return ptr
+
+        def _free(ctx, ptr, nbytes, stream):
+            if ptr in self.live:
+                del self.live[ptr]
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self._a = ALLOC_FN(_alloc)
+        self._f = FREE_FN(_free)
+        self.struct = Alloc(None, self._a, self._f)
+
+
+class Case:
+    """A UGKS case resident on the GPU (one time step = ``ugks_step``)."""
+
+    def __init__(self, mesh, vgrid, params, init=None, precision=FP64, stream=None, torch_alloc=True,
+                 patch_cells=0, vtile=0):
+        L = load()
+        self.D = int(mesh["dim"])
+        self.C = len(mesh["cell_vol"])
+        self.Nv = len(vgrid["w"])
+        self.nc = 2 if self.D == 2 else 1
+        (m, v, p), keep = make_structs(mesh, vgrid, params, init, precision, patch_cells, vtile)
+        self._keep = keep
+        self._alloc = None
+        if torch_alloc:
+            import torch
+            dev = torch.cuda.current_device()
+            self._alloc = _TorchAllocator(dev)
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+        h = ct.c_void_p()
+        check(L.ugks_create(ct.byref(m), ct.byref(v), ct.byref(p),
+                            ct.byref(self._alloc.struct) if self._alloc else None,
+                            ct.c_void_p(stream or 0), ct.byref(h)))
+        self._h = h
+        self.stream = stream
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ugks_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def step(self, n=1):
+        check(load().ugks_step(self._h, int(n)))
+
+    def check(self):
+        check(load().ugks_check(self._h))
+
+    def info(self):
+        i = Info()
+        check(load().ugks_info(self._h, ct.byref(i)))
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def moments(self):
+        rho = np.empty(self.C)
+        U = np.empty((self.C, self.D))
+        T = np.empty(self.C)
+        q = np.empty((self.C, self.D))
+        check(load().ugks_moments(self._h, _p(rho), _p(U), _p(T), _p(q)))
+        return rho, U, T, q
+
+    def residual(self):
+        r = np.empty(self.D + 2)
+        check(load().ugks_residual(self._h, _p(r)))
+        return r
+
+    def state(self, with_f=True):
+        f = np.empty((self.C, self.nc, self.Nv)) if with_f else None
+        W = np.empty((self.C, self.D + 2))
+        check(load().ugks_get_state(self._h, _p(f), _p(W)))
+        return f, W
+
+    def set_state(self, f=None, W=None):
+        fa = _c(f) if f is not None else None
+        Wa = _c(W) if W is not None else None
+        check(load().ugks_set_state(self._h, _p(fa), _p(Wa)))
+
+    def heat_flux(self):
+        return self.moments()[3]
+
+    GROUPS = ("prep", "face", "wall", "gather", "update_W", "collide")
+
+    def profile_begin(self, max_steps):
+        check(load().ugks_profile_begin(self._h, int(max_steps)))
+
+    def profile_end(self):
+        ms = np.zeros(len(self.GROUPS))
+        n = ct.c_int32()
+        check(load().ugks_profile_end(self._h, _p(ms), len(ms), ct.byref(n)))
+        return dict(zip(self.GROUPS, ms)), n.value

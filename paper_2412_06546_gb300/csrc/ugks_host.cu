@@ -1,0 +1,883 @@
+// ugks_host.cu -- C ABI of the UGKS library: validation, host preprocessing
+// (cell ordering, least-squares coefficients, gather patches), device state and
+// the launch sequence of a time step.  The numerics live in ugks_kernels.cu.
+#include "../../include/ugks.h"
+#include "ugks_device.cuh"
+#include "ugks_kernels.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_err;
+
+struct Fail {
+    ugks_status code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(ugks_status code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    throw Fail{code, buf};
+}
+
+void cuda_ok(cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) fail(UGKS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct ugks_case {
+    int D = 0, NC = 0, prec = UGKS_FP64;
+    int64_t C = 0, F = 0, Nv = 0, nvp = 0;
+    int G = 0, NW = 0;
+    double dt = 0.0;
+    int64_t step = 0;
+    cudaStream_t stream = nullptr;
+    ugks_alloc alloc{};
+    bool user_alloc = false;
+    std::vector<std::pair<void *, size_t>> blocks;
+    size_t device_bytes = 0, f_bytes = 0;
+    ugks::DevCase<double> d64{};
+    ugks::DevCase<float> d32{};
+    ugks::StepConfig cfg{};
+    int P = 0, vtile = 0, n_patches = 0, n_vt = 0;
+    long long *perm_d = nullptr;   // caller cell i -> internal cell
+    double *res_d = nullptr;       // [M]
+    int *flags_d = nullptr;
+    int n_res_blocks = 0;
+    bool stepped = false;
+    // kernel-group profiling
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_max = 0, prof_used = 0;
+
+    void *dalloc(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) & ~size_t(255);
+        void *p = nullptr;
+        if (user_alloc) {
+            p = alloc.alloc(alloc.ctx, bytes, (void *)stream);
+            if (!p) fail(UGKS_ENOMEM, "device allocation of %zu bytes failed", bytes);
+        } else {
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                fail(UGKS_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+            }
+        }
+        blocks.push_back({p, bytes});
+        device_bytes += bytes;
+        return p;
+    }
+
+    template <typename V>
+    V *upload(const std::vector<V> &h)
+    {
+        V *d = (V *)dalloc(h.size() * sizeof(V));
+        if (!h.empty()) cuda_ok(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice, stream),
+                                "upload");
+        return d;
+    }
+
+    void release()
+    {
+        if (stream) cudaStreamSynchronize(stream);
+        else cudaDeviceSynchronize();
+        for (auto &b : blocks) {
+            if (user_alloc) alloc.free(alloc.ctx, b.first, b.second, (void *)stream);
+            else cudaFree(b.first);
+        }
+        blocks.clear();
+    }
+};
+
+namespace {
+
+// 2D / 3D Morton key of quantised centroids
+uint64_t spread2(uint64_t x)
+{
+    x &= 0xffffffffULL;
+    x = (x | (x << 16)) & 0x0000ffff0000ffffULL;
+    x = (x | (x << 8)) & 0x00ff00ff00ff00ffULL;
+    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0fULL;
+    x = (x | (x << 2)) & 0x3333333333333333ULL;
+    x = (x | (x << 1)) & 0x5555555555555555ULL;
+    return x;
+}
+
+uint64_t spread3(uint64_t x)
+{
+    x &= 0x1fffffULL;
+    x = (x | (x << 32)) & 0x1f00000000ffffULL;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+
+struct Host {
+    // internal-order geometry produced by preprocessing
+    std::vector<int> perm_i2u, perm_u2i;
+    std::vector<int> cf_ptr, cf_face;
+    std::vector<signed char> cf_side;
+    std::vector<double> cf_r, cf_coef;
+    std::vector<short> cf_sL, cf_sR;
+    std::vector<int> nb_ptr, nb_id;
+    std::vector<double> nb_a, eps2, vol;
+    std::vector<int> fL, fR, faux, ftag, gface, wface;
+    std::vector<signed char> ftype;
+    std::vector<double> fn, frL, frR;
+    std::vector<int> ring_ptr, ring_cells;
+    int max_slope = 0;
+    double hmin = INFINITY;
+};
+
+void validate(const ugks_mesh *m, const ugks_vgrid *v, const ugks_params *p)
+{
+    if (!m || !v || !p) fail(UGKS_EINVAL, "mesh, vgrid and params must not be NULL");
+    if (m->dim != 2 && m->dim != 3) fail(UGKS_EINVAL, "mesh dim must be 2 or 3 (got %d)", m->dim);
+    if (v->dim != m->dim) fail(UGKS_EINVAL, "velocity grid dim %d != mesh dim %d", v->dim, m->dim);
+    if (m->n_cells <= 0 || m->n_faces < 0) fail(UGKS_EINVAL, "mesh needs n_cells > 0, n_faces >= 0");
+    if (m->n_cells > (1LL << 30) || m->n_faces > (1LL << 30)) fail(UGKS_EINVAL, "mesh too large for 32-bit indexing");
+    if (v->nv <= 0 || v->nv > (1 << 24)) fail(UGKS_EINVAL, "velocity count %lld out of range", (long long)v->nv);
+    if (!m->cell_xc || !m->cell_vol || !m->face_cells || !m->face_n || !m->face_S || !m->face_xc ||
+        !m->face_type || !m->face_tag)
+        fail(UGKS_EINVAL, "mesh arrays must not be NULL");
+    if (!v->u || !v->w) fail(UGKS_EINVAL, "velocity arrays must not be NULL");
+    if (p->precision != UGKS_FP64 && p->precision != UGKS_FP32) fail(UGKS_EINVAL, "unknown precision %d", p->precision);
+    if (!(p->Pr > 0.0) || !(p->omega >= 0.0) || !(p->L_ref > 0.0) || !(p->Kn > 0.0))
+        fail(UGKS_EINVAL, "need Kn > 0, L_ref > 0, Pr > 0, omega >= 0");
+    if (!(p->dt > 0.0) && !(p->cfl > 0.0)) fail(UGKS_EINVAL, "need cfl > 0 or dt > 0");
+    if (p->limiter && !(p->venkat_K > 0.0)) fail(UGKS_EINVAL, "venkat_K must be > 0 with the limiter on");
+    if (p->n_walls < 0 || (p->n_walls > 0 && (!p->wall_T || !p->wall_U))) fail(UGKS_EINVAL, "wall arrays missing");
+    for (int i = 0; i < p->n_walls; ++i)
+        if (!(p->wall_T[i] > 0.0)) fail(UGKS_EINVAL, "wall %d temperature must be > 0", i);
+    const int D = m->dim;
+    for (int64_t i = 0; i < m->n_cells; ++i)
+        if (!(m->cell_vol[i] > 0.0)) fail(UGKS_EINVAL, "cell %lld has non-positive volume", (long long)i);
+    bool farfield = false;
+    for (int64_t f = 0; f < m->n_faces; ++f) {
+        const int64_t a = m->face_cells[2 * f], b = m->face_cells[2 * f + 1];
+        const int t = m->face_type[f];
+        if (a < 0 || a >= m->n_cells) fail(UGKS_EINVAL, "face %lld: owner out of range", (long long)f);
+        if (t == UGKS_FACE_INTERIOR || t == UGKS_FACE_PERIODIC) {
+            if (b < 0 || b >= m->n_cells) fail(UGKS_EINVAL, "face %lld: neighbour out of range", (long long)f);
+            if (t == UGKS_FACE_PERIODIC && !m->face_shift) fail(UGKS_EINVAL, "periodic faces need face_shift");
+        } else if (t == UGKS_FACE_WALL || t == UGKS_FACE_FARFIELD) {
+            if (b != -1) fail(UGKS_EINVAL, "face %lld: boundary face must have neighbour -1", (long long)f);
+            if (t == UGKS_FACE_WALL && (m->face_tag[f] < 0 || m->face_tag[f] >= p->n_walls))
+                fail(UGKS_EINVAL, "face %lld: wall tag %d out of range", (long long)f, m->face_tag[f]);
+            if (t == UGKS_FACE_FARFIELD) farfield = true;
+        } else {
+            fail(UGKS_EINVAL, "face %lld: unknown type %d", (long long)f, t);
+        }
+        if (!(m->face_S[f] > 0.0)) fail(UGKS_EINVAL, "face %lld: area must be > 0", (long long)f);
+        double nn = 0.0;
+        for (int d = 0; d < D; ++d) nn += m->face_n[f * D + d] * m->face_n[f * D + d];
+        if (std::fabs(nn - 1.0) > 1e-8) fail(UGKS_EINVAL, "face %lld: normal is not unit length", (long long)f);
+    }
+    if (farfield && (!(p->inf_rho > 0.0) || !(p->inf_T > 0.0)))
+        fail(UGKS_EINVAL, "far-field faces need inf_rho > 0 and inf_T > 0");
+    for (int64_t k = 0; k < v->nv; ++k)
+        if (!(v->w[k] >= 0.0) || !std::isfinite(v->w[k])) fail(UGKS_EINVAL, "velocity weight %lld invalid", (long long)k);
+    if (p->prim_init)
+        for (int64_t i = 0; i < m->n_cells; ++i)
+            if (!(p->prim_init[i * (D + 2)] > 0.0) || !(p->prim_init[i * (D + 2) + D + 1] > 0.0))
+                fail(UGKS_EINVAL, "initial state of cell %lld needs rho > 0 and T > 0", (long long)i);
+    if (p->vtile != 0 && p->vtile != 32 && p->vtile != 64 && p->vtile != 128)
+        fail(UGKS_EINVAL, "vtile must be 0, 32, 64 or 128");
+    if (p->patch_cells < 0 || p->patch_cells > 4096) fail(UGKS_EINVAL, "patch_cells out of range");
+}
+
+// invert the DxD normal matrix by its adjugate
+bool invert_small(int D, const double *A, double *Ainv)
+{
+    double tr = 0.0;
+    for (int a = 0; a < D; ++a) tr += A[a * D + a];
+    double det;
+    if (D == 2) {
+        det = A[0] * A[3] - A[1] * A[2];
+        if (!(std::fabs(det) > 1e-12 * std::pow(tr / D, D))) return false;
+        Ainv[0] = A[3] / det;
+        Ainv[1] = -A[1] / det;
+        Ainv[2] = -A[2] / det;
+        Ainv[3] = A[0] / det;
+        return true;
+    }
+    const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    if (!(std::fabs(det) > 1e-12 * std::pow(tr / D, D))) return false;
+    Ainv[0] = c00 / det;
+    Ainv[3] = c01 / det;
+    Ainv[6] = c02 / det;
+    Ainv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    Ainv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    Ainv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    Ainv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    Ainv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    Ainv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+    return true;
+}
+
+void preprocess(const ugks_mesh *m, const ugks_params *p, int P, Host &h)
+{
+    const int D = m->dim;
+    const int C = (int)m->n_cells, F = (int)m->n_faces;
+    // ---- cell order: Morton order of the centroids (spatially compact patches)
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < C; ++i)
+        for (int d = 0; d < D; ++d) {
+            lo[d] = std::min(lo[d], m->cell_xc[(size_t)i * D + d]);
+            hi[d] = std::max(hi[d], m->cell_xc[(size_t)i * D + d]);
+        }
+    std::vector<uint64_t> key(C);
+    const double bits = D == 2 ? 4294967295.0 : 2097151.0;
+    for (int i = 0; i < C; ++i) {
+        uint64_t k = 0;
+        for (int d = 0; d < D; ++d) {
+            double span = hi[d] - lo[d];
+            double t = span > 0 ? (m->cell_xc[(size_t)i * D + d] - lo[d]) / span : 0.0;
+            uint64_t qv = (uint64_t)std::llround(t * bits);
+            k |= (D == 2 ? spread2(qv) : spread3(qv)) << d;
+        }
+        key[i] = k;
+    }
+    h.perm_i2u.resize(C);
+    std::iota(h.perm_i2u.begin(), h.perm_i2u.end(), 0);
+    std::stable_sort(h.perm_i2u.begin(), h.perm_i2u.end(), [&](int a, int b) { return key[a] < key[b]; });
+    h.perm_u2i.resize(C);
+    for (int i = 0; i < C; ++i) h.perm_u2i[h.perm_i2u[i]] = i;
+    auto X = [&](int ci, int d) { return m->cell_xc[(size_t)h.perm_i2u[ci] * D + d]; };
+    h.vol.resize(C);
+    for (int i = 0; i < C; ++i) h.vol[i] = m->cell_vol[h.perm_i2u[i]];
+
+    // ---- faces
+    h.fL.assign(F, -1);
+    h.fR.assign(F, -1);
+    h.faux.assign(F, -1);
+    h.ftag.assign(F, 0);
+    h.ftype.assign(F, 0);
+    h.fn.assign((size_t)F * D, 0.0);
+    h.frL.assign((size_t)F * D, 0.0);
+    h.frR.assign((size_t)F * D, 0.0);
+    for (int f = 0; f < F; ++f) {
+        const int t = m->face_type[f];
+        h.ftype[f] = (signed char)t;
+        h.ftag[f] = m->face_tag[f];
+        h.fL[f] = h.perm_u2i[m->face_cells[2 * f]];
+        if (t == UGKS_FACE_INTERIOR || t == UGKS_FACE_PERIODIC) h.fR[f] = h.perm_u2i[m->face_cells[2 * f + 1]];
+        for (int d = 0; d < D; ++d) {
+            h.fn[(size_t)f * D + d] = m->face_n[(size_t)f * D + d];
+            const double xf = m->face_xc[(size_t)f * D + d];
+            h.frL[(size_t)f * D + d] = xf - X(h.fL[f], d);
+            if (h.fR[f] >= 0) {
+                const double sh = (t == UGKS_FACE_PERIODIC) ? m->face_shift[(size_t)f * D + d] : 0.0;
+                h.frR[(size_t)f * D + d] = xf - sh - X(h.fR[f], d);
+            }
+        }
+        if (t == UGKS_FACE_FARFIELD) {
+            h.faux[f] = (int)h.gface.size();
+            h.gface.push_back(f);
+        } else if (t == UGKS_FACE_WALL) {
+            h.faux[f] = (int)h.wface.size();
+            h.wface.push_back(f);
+        }
+    }
+
+    // ---- faces of each cell (CSR, face order within a cell)
+    h.cf_ptr.assign(C + 1, 0);
+    for (int f = 0; f < F; ++f) {
+        h.cf_ptr[h.fL[f] + 1]++;
+        if (h.fR[f] >= 0) h.cf_ptr[h.fR[f] + 1]++;
+    }
+    for (int i = 0; i < C; ++i) h.cf_ptr[i + 1] += h.cf_ptr[i];
+    const int ncf = h.cf_ptr[C];
+    h.cf_face.resize(ncf);
+    h.cf_side.resize(ncf);
+    h.cf_r.resize((size_t)ncf * D);
+    h.cf_coef.resize(ncf);
+    std::vector<int> fill(C, 0);
+    for (int f = 0; f < F; ++f)
+        for (int s = 0; s < 2; ++s) {
+            const int c = s == 0 ? h.fL[f] : h.fR[f];
+            if (c < 0) continue;
+            const int e = h.cf_ptr[c] + fill[c]++;
+            h.cf_face[e] = f;
+            h.cf_side[e] = (signed char)s;
+            for (int d = 0; d < D; ++d) h.cf_r[(size_t)e * D + d] = s == 0 ? h.frL[(size_t)f * D + d] : h.frR[(size_t)f * D + d];
+            h.cf_coef[e] = (s == 0 ? -1.0 : 1.0) * m->face_S[f] / h.vol[c];
+        }
+
+    // ---- least squares: neighbours across non-wall faces, far-field ghosts
+    //      mirrored across the face; weights 1/|d|^2; a = w M^{-1} d
+    h.nb_ptr.assign(C + 1, 0);
+    h.eps2.resize(C);
+    std::vector<double> dvec;
+    for (int c = 0; c < C; ++c) {
+        double sumS = 0.0;
+        const int n0 = (int)h.nb_id.size();
+        for (int e = h.cf_ptr[c]; e < h.cf_ptr[c + 1]; ++e) {
+            const int f = h.cf_face[e];
+            sumS += m->face_S[f];
+            const int t = h.ftype[f];
+            if (t == UGKS_FACE_WALL) continue;
+            double d[3];
+            if (t == UGKS_FACE_FARFIELD) {
+                double rn = 0.0;
+                for (int k = 0; k < D; ++k) rn += h.frL[(size_t)f * D + k] * h.fn[(size_t)f * D + k];
+                for (int k = 0; k < D; ++k) d[k] = 2.0 * rn * h.fn[(size_t)f * D + k];
+                h.nb_id.push_back(-(h.faux[f] + 1));
+            } else {
+                // vector from this cell to the other one through the face
+                const bool own = h.cf_side[e] == 0;
+                const int o = own ? h.fR[f] : h.fL[f];
+                for (int k = 0; k < D; ++k) {
+                    const double ro = own ? h.frR[(size_t)f * D + k] : h.frL[(size_t)f * D + k];
+                    d[k] = h.cf_r[(size_t)e * D + k] - ro;
+                }
+                h.nb_id.push_back(o);
+            }
+            for (int k = 0; k < D; ++k) dvec.push_back(d[k]);
+        }
+        const int n1 = (int)h.nb_id.size();
+        h.nb_ptr[c + 1] = n1;
+        double A[9] = {0}, Ai[9];
+        for (int q = n0; q < n1; ++q) {
+            const double *d = &dvec[(size_t)q * D];
+            double dd = 0.0;
+            for (int k = 0; k < D; ++k) dd += d[k] * d[k];
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) A[a * D + b] += d[a] * d[b] / dd;
+        }
+        const bool ok = n1 > n0 && invert_small(D, A, Ai);
+        for (int q = n0; q < n1; ++q) {
+            const double *d = &dvec[(size_t)q * D];
+            double dd = 0.0;
+            for (int k = 0; k < D; ++k) dd += d[k] * d[k];
+            for (int a = 0; a < D; ++a) {
+                double s = 0.0;
+                if (ok)
+                    for (int b = 0; b < D; ++b) s += Ai[a * D + b] * d[b];
+                h.nb_a.push_back(s / dd);
+            }
+        }
+        // limiter scale h_c = 2 D |Omega_c| / sum S; time-step scale
+        // 2 |Omega_c| / sum S bounds |Omega_c| / sum_f S_f (u.n)^+ for |u| = 1
+        const double hc = 2.0 * D * h.vol[c] / sumS;
+        h.hmin = std::min(h.hmin, 2.0 * h.vol[c] / sumS);
+        const double Kh = p->venkat_K * hc;
+        h.eps2[c] = Kh * Kh * Kh;
+    }
+
+    // ---- gather patches: P consecutive cells + their face neighbours (ring)
+    const int np = (C + P - 1) / P;
+    h.ring_ptr.assign(np + 1, 0);
+    h.cf_sL.assign(ncf, -1);
+    h.cf_sR.assign(ncf, -1);
+    std::vector<int> slot_of(C, -1);
+    for (int pi = 0; pi < np; ++pi) {
+        const int cb = pi * P, ce = std::min(C, cb + P);
+        for (int c = cb; c < ce; ++c) slot_of[c] = c - cb;
+        int ns = ce - cb;
+        std::vector<int> ring;
+        for (int c = cb; c < ce; ++c)
+            for (int e = h.cf_ptr[c]; e < h.cf_ptr[c + 1]; ++e) {
+                const int f = h.cf_face[e];
+                for (int o : {h.fL[f], h.fR[f]})
+                    if (o >= 0 && slot_of[o] < 0) {
+                        slot_of[o] = ns++;
+                        ring.push_back(o);
+                    }
+            }
+        for (int c = cb; c < ce; ++c)
+            for (int e = h.cf_ptr[c]; e < h.cf_ptr[c + 1]; ++e) {
+                const int f = h.cf_face[e];
+                h.cf_sL[e] = (short)slot_of[h.fL[f]];
+                h.cf_sR[e] = (short)(h.fR[f] >= 0 ? slot_of[h.fR[f]] : -1);
+            }
+        h.max_slope = std::max(h.max_slope, ns);
+        h.ring_cells.insert(h.ring_cells.end(), ring.begin(), ring.end());
+        h.ring_ptr[pi + 1] = (int)h.ring_cells.size();
+        for (int c = cb; c < ce; ++c) slot_of[c] = -1;
+        for (int o : ring) slot_of[o] = -1;
+    }
+    if (h.max_slope > 32767) fail(UGKS_EINVAL, "patch too large");
+}
+
+template <typename T>
+std::vector<T> cast(const std::vector<double> &v)
+{
+    return std::vector<T>(v.begin(), v.end());
+}
+
+template <typename T>
+void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugks_vgrid *v, const ugks_params *p,
+               const Host &h)
+{
+    const int D = c->D, M = D + 2;
+    dc.D = D;
+    dc.NC = c->NC;
+    dc.C = (int)c->C;
+    dc.F = (int)c->F;
+    dc.G = c->G;
+    dc.NW = c->NW;
+    dc.nv = (int)c->Nv;
+    dc.nvp = (int)c->nvp;
+    dc.dt = c->dt;
+    dc.Pr = p->Pr;
+    dc.omega = p->omega;
+    dc.nxi = 3.0 - D;
+    dc.mu_ref = std::isinf(p->Kn) ? INFINITY
+                                  : 15.0 * std::sqrt(2.0 * M_PI) * p->Kn * p->L_ref /
+                                        (2.0 * (5.0 - 2.0 * p->omega) * (7.0 - 2.0 * p->omega));
+    dc.limiter = p->limiter ? 1 : 0;
+    // velocities, padded with u = 0, w = 0
+    for (int d = 0; d < 3; ++d) {
+        dc.ud[d] = nullptr;
+        dc.u[d] = nullptr;
+    }
+    for (int d = 0; d < D; ++d) {
+        std::vector<double> ud(c->nvp, 0.0);
+        for (int64_t k = 0; k < c->Nv; ++k) ud[k] = v->u[k * D + d];
+        dc.ud[d] = c->upload(ud);
+        dc.u[d] = c->upload(cast<T>(ud));
+    }
+    std::vector<double> wd(c->nvp, 0.0);
+    for (int64_t k = 0; k < c->Nv; ++k) wd[k] = v->w[k];
+    dc.wd = c->upload(wd);
+    dc.w = c->upload(cast<T>(wd));
+    // state
+    const size_t fcount = (size_t)c->C * c->NC * c->nvp;
+    dc.f_cur = (T *)c->dalloc(fcount * sizeof(T));
+    dc.f_nxt = (T *)c->dalloc(fcount * sizeof(T));
+    c->f_bytes = fcount * sizeof(T);
+    std::vector<double> W((size_t)c->C * M);
+    for (int64_t i = 0; i < c->C; ++i) {
+        const int ci = h.perm_u2i[i];
+        double pr[5];
+        if (p->prim_init) {
+            for (int k = 0; k < M; ++k) pr[k] = p->prim_init[i * M + k];
+        } else {
+            pr[0] = p->inf_rho;
+            for (int d = 0; d < D; ++d) pr[1 + d] = p->inf_U[d];
+            pr[D + 1] = p->inf_T;
+        }
+        double ke = 0.0;
+        W[(size_t)ci * M] = pr[0];
+        for (int d = 0; d < D; ++d) {
+            W[(size_t)ci * M + 1 + d] = pr[0] * pr[1 + d];
+            ke += pr[1 + d] * pr[1 + d];
+        }
+        W[(size_t)ci * M + D + 1] = pr[0] * (0.5 * ke + 1.5 * pr[D + 1]);
+    }
+    dc.W = c->upload(W);
+    dc.q = (double *)c->dalloc((size_t)c->C * D * sizeof(double));
+    dc.gradW = (double *)c->dalloc((size_t)c->C * D * M * sizeof(double));
+    dc.vol = c->upload(h.vol);
+    dc.nb_ptr = c->upload(h.nb_ptr);
+    dc.nb_id = c->upload(h.nb_id);
+    dc.nb_a_d = c->upload(h.nb_a);
+    dc.nb_a = c->upload(cast<T>(h.nb_a));
+    dc.cf_ptr = c->upload(h.cf_ptr);
+    dc.cf_face = c->upload(h.cf_face);
+    dc.cf_side = c->upload(h.cf_side);
+    dc.cf_r_d = c->upload(h.cf_r);
+    dc.cf_r = c->upload(cast<T>(h.cf_r));
+    dc.cf_coef = c->upload(cast<T>(h.cf_coef));
+    dc.cf_sL = c->upload(h.cf_sL);
+    dc.cf_sR = c->upload(h.cf_sR);
+    dc.eps2_d = c->upload(h.eps2);
+    dc.eps2 = c->upload(cast<T>(h.eps2));
+    dc.fL = c->upload(h.fL);
+    dc.fR = c->upload(h.fR);
+    dc.faux = c->upload(h.faux);
+    dc.ftype = c->upload(h.ftype);
+    dc.ftag = c->upload(h.ftag);
+    dc.fn_d = c->upload(h.fn);
+    dc.frL_d = c->upload(h.frL);
+    dc.frR_d = c->upload(h.frR);
+    dc.fn = c->upload(cast<T>(h.fn));
+    dc.gface = c->upload(h.gface);
+    dc.Wg = (double *)c->dalloc((size_t)std::max(c->G, 1) * M * sizeof(double));
+    dc.grec = (T *)c->dalloc((size_t)std::max(c->G, 1) * ugks::GREC * sizeof(T));
+    dc.wface = c->upload(h.wface);
+    std::vector<double> wT(std::max(p->n_walls, 1), 1.0), wU(3 * std::max(p->n_walls, 1), 0.0);
+    for (int i = 0; i < p->n_walls; ++i) {
+        wT[i] = p->wall_T[i];
+        for (int d = 0; d < 3; ++d) wU[3 * i + d] = p->wall_U[3 * i + d];
+    }
+    dc.wallT = c->upload(wT);
+    dc.wallU = c->upload(wU);
+    {
+        double ke = 0.0;
+        dc.inf_W[0] = p->inf_rho;
+        for (int d = 0; d < D; ++d) {
+            dc.inf_W[1 + d] = p->inf_rho * p->inf_U[d];
+            ke += p->inf_U[d] * p->inf_U[d];
+        }
+        dc.inf_W[D + 1] = p->inf_rho * (0.5 * ke + 1.5 * p->inf_T);
+    }
+    dc.rho_w = (double *)c->dalloc((size_t)std::max(c->NW, 1) * sizeof(double));
+    dc.wrec = (T *)c->dalloc((size_t)std::max(c->NW, 1) * ugks::GREC * sizeof(T));
+    dc.crec = (T *)c->dalloc((size_t)c->C * ugks::CREC * sizeof(T));
+    dc.krec = (T *)c->dalloc((size_t)c->C * ugks::CREC * sizeof(T));
+    const size_t Fm = (size_t)std::max<int64_t>(c->F, 1);
+    dc.frec = (T *)c->dalloc(Fm * ugks::FREC * sizeof(T));
+    dc.fside = (T *)c->dalloc(Fm * 2 * ugks::GREC * sizeof(T));
+    dc.fdW0 = (double *)c->dalloc(Fm * D * M * sizeof(double));
+    dc.fq0 = (double *)c->dalloc(Fm * D * sizeof(double));
+    dc.fUref = (double *)c->dalloc(Fm * D * sizeof(double));
+    dc.fsum1 = (double *)c->dalloc(Fm * M * sizeof(double));
+    const int NS = M * (M + 1) / 2;
+    dc.fsum2 = (double *)c->dalloc(Fm * NS * (D + 1) * sizeof(double));
+    dc.fprim0 = (double *)c->dalloc(Fm * M * sizeof(double));
+    dc.dW_part = (double *)c->dalloc((size_t)c->C * c->n_vt * M * sizeof(double));
+    dc.res_part = (double *)c->dalloc((size_t)c->n_res_blocks * 2 * M * sizeof(double));
+    dc.flags = c->flags_d;
+    dc.P = c->P;
+    dc.n_patches = c->n_patches;
+    dc.n_vt = c->n_vt;
+    dc.vtile = c->vtile;
+    dc.ring_ptr = c->upload(h.ring_ptr);
+    dc.ring_cells = c->upload(h.ring_cells);
+}
+
+}  // namespace
+
+namespace {
+ugks_status guard(const std::function<void()> &fn)
+{
+    try {
+        g_err.clear();
+        fn();
+        return UGKS_OK;
+    } catch (const Fail &e) {
+        g_err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        return UGKS_ENOMEM;
+    } catch (const std::exception &e) {
+        g_err = e.what();
+        return UGKS_EINVAL;
+    } catch (...) {
+        g_err = "unknown error";
+        return UGKS_EINVAL;
+    }
+}
+
+template <typename Fn>
+auto with_dc(ugks_case *c, Fn &&fn)
+{
+    if (c->prec == UGKS_FP64) return fn(c->d64);
+    return fn(c->d32);
+}
+}  // namespace
+
+extern "C" {
+
+const char *ugks_last_error(void) { return g_err.c_str(); }
+
+ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ugks_params *params,
+                        const ugks_alloc *alloc, void *stream, ugks_case **out)
+{
+    if (!out) {
+        g_err = "out must not be NULL";
+        return UGKS_EINVAL;
+    }
+    *out = nullptr;
+    std::unique_ptr<ugks_case> c(new ugks_case());
+    ugks_status st = guard([&] {
+        validate(mesh, vgrid, params);
+        if (alloc && (!alloc->alloc || !alloc->free)) fail(UGKS_EINVAL, "allocator callbacks missing");
+        c->D = mesh->dim;
+        c->NC = mesh->dim == 2 ? 2 : 1;
+        c->prec = params->precision;
+        c->C = mesh->n_cells;
+        c->F = mesh->n_faces;
+        c->Nv = vgrid->nv;
+        c->stream = (cudaStream_t)stream;
+        if (alloc) {
+            c->alloc = *alloc;
+            c->user_alloc = true;
+        }
+        const size_t esz = c->prec == UGKS_FP64 ? 8 : 4;
+        // tiling: velocity tile of 32*TV, patch of P cells sized to shared memory
+        c->vtile = params->vtile > 0 ? params->vtile : 32;
+        int P = params->patch_cells > 0 ? params->patch_cells : (c->prec == UGKS_FP64 ? 32 : 64);
+        Host h;
+        int dev = 0;
+        cuda_ok(cudaGetDevice(&dev), "cudaGetDevice");
+        int smem_max = 0;
+        cuda_ok(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem attr");
+        for (;;) {
+            h = Host();
+            preprocess(mesh, params, P, h);
+            const size_t smem = (size_t)h.max_slope * c->NC * c->D * c->vtile * esz;
+            if (smem <= (size_t)smem_max || P <= 4) {
+                if (smem > (size_t)smem_max) fail(UGKS_EINVAL, "mesh stencil too large for shared memory");
+                c->cfg.smem = smem;
+                break;
+            }
+            P = std::max(4, P / 2);
+        }
+        c->P = P;
+        c->n_patches = (int)((c->C + P - 1) / P);
+        c->nvp = (c->Nv + c->vtile - 1) / c->vtile * c->vtile;
+        c->n_vt = (int)(c->nvp / c->vtile);
+        c->G = (int)h.gface.size();
+        c->NW = (int)h.wface.size();
+        c->dt = params->dt > 0.0 ? params->dt : [&] {
+            double umax = 0.0;
+            for (int64_t k = 0; k < c->Nv; ++k) {
+                double s = 0.0;
+                for (int d = 0; d < c->D; ++d) s += vgrid->u[k * c->D + d] * vgrid->u[k * c->D + d];
+                umax = std::max(umax, std::sqrt(s));
+            }
+            return params->cfl * h.hmin / umax;   // upwind CFL bound (Alg. 1 line 1)
+        }();
+        c->n_res_blocks = (int)((c->C + 255) / 256);
+        c->cfg.n_res_blocks = c->n_res_blocks;
+        c->flags_d = (int *)c->dalloc(sizeof(int));
+        cuda_ok(cudaMemsetAsync(c->flags_d, 0, sizeof(int), c->stream), "memset");
+        c->res_d = (double *)c->dalloc(8 * sizeof(double));
+        cuda_ok(cudaMemsetAsync(c->res_d, 0, 8 * sizeof(double), c->stream), "memset");
+        std::vector<long long> perm(h.perm_u2i.begin(), h.perm_u2i.end());
+        c->perm_d = c->upload(perm);
+        if (c->prec == UGKS_FP64) {
+            fill_case<double>(c.get(), c->d64, mesh, vgrid, params, h);
+            cuda_ok(ugks::launch_init(c->d64, c->stream), "init");
+        } else {
+            fill_case<float>(c.get(), c->d32, mesh, vgrid, params, h);
+            cuda_ok(ugks::launch_init(c->d32, c->stream), "init");
+        }
+        cuda_ok(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "create sync");
+    });
+    if (st != UGKS_OK) {
+        std::string keep = g_err;
+        c->release();
+        g_err = keep;
+        return st;
+    }
+    *out = c.release();
+    return UGKS_OK;
+}
+
+ugks_status ugks_step(ugks_case *c, int32_t nsteps)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        if (nsteps < 0) fail(UGKS_EINVAL, "nsteps must be >= 0");
+        for (int32_t s = 0; s < nsteps; ++s) {
+            cudaEvent_t *ev = nullptr;
+            if (c->prof_used < c->prof_max) ev = &c->prof_ev[(size_t)c->prof_used++ * (ugks::N_GROUPS + 1)];
+            with_dc(c, [&](auto &dc) { cuda_ok(ugks::launch_step(dc, c->cfg, c->stream, ev), "step launch"); });
+            ++c->step;
+            c->stepped = true;
+        }
+    });
+}
+
+ugks_status ugks_check(ugks_case *c)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        const int M = c->D + 2;
+        double *W = c->prec == UGKS_FP64 ? c->d64.W : c->d32.W;
+        cuda_ok(ugks::launch_check(W, (int)c->C, M, c->flags_d, c->stream), "check launch");
+        int flag = 0;
+        cuda_ok(cudaMemcpyAsync(&flag, c->flags_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "check copy");
+        cuda_ok(cudaStreamSynchronize(c->stream), "check sync");
+        if (flag) fail(UGKS_ENUMERIC, "non-finite or non-positive density / temperature in the state");
+    });
+}
+
+ugks_status ugks_moments(ugks_case *c, double *rho, double *U, double *T, double *q)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        const int D = c->D;
+        const size_t per = 2 * D + 2;
+        double *Wd = c->prec == UGKS_FP64 ? c->d64.W : c->d32.W;
+        double *qd = c->prec == UGKS_FP64 ? c->d64.q : c->d32.q;
+        // reuse the gradient buffer as staging ([C][D][D+2] >= [C][2D+2])
+        double *out = c->prec == UGKS_FP64 ? c->d64.gradW : c->d32.gradW;
+        cuda_ok(ugks::launch_moments_out(Wd, qd, c->perm_d, (int)c->C, D, out, c->stream), "moments launch");
+        std::vector<double> hbuf((size_t)c->C * per);
+        cuda_ok(cudaMemcpyAsync(hbuf.data(), out, hbuf.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                "moments copy");
+        cuda_ok(cudaStreamSynchronize(c->stream), "moments sync");
+        for (int64_t i = 0; i < c->C; ++i) {
+            const double *o = &hbuf[(size_t)i * per];
+            if (rho) rho[i] = o[0];
+            for (int d = 0; d < D; ++d) {
+                if (U) U[i * D + d] = o[1 + d];
+                if (q) q[i * D + d] = o[D + 2 + d];
+            }
+            if (T) T[i] = o[D + 1];
+        }
+    });
+}
+
+ugks_status ugks_residual(ugks_case *c, double *res)
+{
+    return guard([&] {
+        if (!c || !res) fail(UGKS_EINVAL, "case and res must not be NULL");
+        const int M = c->D + 2;
+        if (!c->stepped) {
+            for (int m = 0; m < M; ++m) res[m] = 0.0;
+            return;
+        }
+        const double *rp = c->prec == UGKS_FP64 ? c->d64.res_part : c->d32.res_part;
+        cuda_ok(ugks::launch_residual(rp, c->n_res_blocks, c->D, c->res_d, c->stream), "residual launch");
+        cuda_ok(cudaMemcpyAsync(res, c->res_d, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "residual copy");
+        cuda_ok(cudaStreamSynchronize(c->stream), "residual sync");
+    });
+}
+
+ugks_status ugks_get_state(ugks_case *c, double *f, double *W)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        const int D = c->D, M = D + 2;
+        if (W) {
+            double *Wd = c->prec == UGKS_FP64 ? c->d64.W : c->d32.W;
+            double *stg = c->prec == UGKS_FP64 ? c->d64.gradW : c->d32.gradW;
+            cuda_ok(ugks::launch_W_permute(Wd, c->perm_d, (int)c->C, D, stg, 0, c->stream), "W export");
+            cuda_ok(cudaMemcpyAsync(W, stg, (size_t)c->C * M * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                    "W copy");
+            cuda_ok(cudaStreamSynchronize(c->stream), "sync");
+        }
+        if (f) {
+            // stage through the f_nxt buffer in chunks of cells
+            const size_t per = (size_t)c->NC * c->Nv;
+            const size_t cap = c->f_bytes / sizeof(double);
+            const int chunk = (int)std::max<size_t>(1, std::min<size_t>(cap / per, (size_t)c->C));
+            for (int c0 = 0; c0 < (int)c->C; c0 += chunk) {
+                const int nc = (int)std::min<int64_t>(chunk, c->C - c0);
+                with_dc(c, [&](auto &dc) {
+                    double *stg = (double *)dc.f_nxt;
+                    cuda_ok(ugks::launch_f_export(dc, c->perm_d, c0, nc, stg, c->stream), "f export");
+                    cuda_ok(cudaMemcpyAsync(f + (size_t)c0 * per, stg, (size_t)nc * per * sizeof(double),
+                                            cudaMemcpyDeviceToHost, c->stream),
+                            "f copy");
+                    cuda_ok(cudaStreamSynchronize(c->stream), "sync");
+                });
+            }
+        }
+    });
+}
+
+ugks_status ugks_set_state(ugks_case *c, const double *f, const double *W)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        const int D = c->D, M = D + 2;
+        if (W) {
+            double *Wd = c->prec == UGKS_FP64 ? c->d64.W : c->d32.W;
+            double *stg = c->prec == UGKS_FP64 ? c->d64.gradW : c->d32.gradW;
+            cuda_ok(cudaMemcpyAsync(stg, W, (size_t)c->C * M * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                    "W upload");
+            cuda_ok(ugks::launch_W_permute(stg, c->perm_d, (int)c->C, D, Wd, 1, c->stream), "W import");
+        }
+        if (f) {
+            const size_t per = (size_t)c->NC * c->Nv;
+            const size_t cap = c->f_bytes / sizeof(double);
+            const int chunk = (int)std::max<size_t>(1, std::min<size_t>(cap / per, (size_t)c->C));
+            for (int c0 = 0; c0 < (int)c->C; c0 += chunk) {
+                const int nc = (int)std::min<int64_t>(chunk, c->C - c0);
+                with_dc(c, [&](auto &dc) {
+                    double *stg = (double *)dc.f_nxt;
+                    cuda_ok(cudaMemcpyAsync(stg, f + (size_t)c0 * per, (size_t)nc * per * sizeof(double),
+                                            cudaMemcpyHostToDevice, c->stream),
+                            "f upload");
+                    cuda_ok(ugks::launch_f_import(dc, c->perm_d, c0, nc, stg, c->stream), "f import");
+                });
+            }
+        }
+        if (f || W) with_dc(c, [&](auto &dc) { cuda_ok(ugks::launch_heatflux(dc, c->stream), "heat flux"); });
+    });
+}
+
+ugks_status ugks_profile_begin(ugks_case *c, int32_t max_steps)
+{
+    return guard([&] {
+        if (!c || max_steps < 0) fail(UGKS_EINVAL, "invalid profile request");
+        for (auto e : c->prof_ev) cudaEventDestroy(e);
+        c->prof_ev.assign((size_t)max_steps * (ugks::N_GROUPS + 1), nullptr);
+        for (auto &e : c->prof_ev) cuda_ok(cudaEventCreate(&e), "event create");
+        c->prof_max = max_steps;
+        c->prof_used = 0;
+    });
+}
+
+ugks_status ugks_profile_end(ugks_case *c, double *ms, int32_t n, int32_t *steps)
+{
+    return guard([&] {
+        if (!c || !ms) fail(UGKS_EINVAL, "invalid profile request");
+        cuda_ok(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "profile sync");
+        for (int i = 0; i < n; ++i) ms[i] = 0.0;
+        for (int s = 0; s < c->prof_used; ++s)
+            for (int g = 0; g < ugks::N_GROUPS && g < n; ++g) {
+                float t = 0.f;
+                cudaEvent_t *e = &c->prof_ev[(size_t)s * (ugks::N_GROUPS + 1)];
+                cuda_ok(cudaEventElapsedTime(&t, e[g], e[g + 1]), "event time");
+                ms[g] += t;
+            }
+        if (steps) *steps = c->prof_used;
+        for (auto e : c->prof_ev) cudaEventDestroy(e);
+        c->prof_ev.clear();
+        c->prof_max = c->prof_used = 0;
+    });
+}
+
+ugks_status ugks_info(const ugks_case *c, ugks_info_t *info)
+{
+    return guard([&] {
+        if (!c || !info) fail(UGKS_EINVAL, "case and info must not be NULL");
+        info->dim = c->D;
+        info->ncomp = c->NC;
+        info->precision = c->prec;
+        info->n_cells = c->C;
+        info->n_faces = c->F;
+        info->nv = c->Nv;
+        info->nv_pad = c->nvp;
+        info->dt = c->dt;
+        info->step = c->step;
+        info->device_bytes = c->device_bytes;
+        info->f_bytes = c->f_bytes;
+        info->n_patches = c->n_patches;
+        info->patch_cells = c->P;
+        info->vtile = c->vtile;
+        info->kernel_launches_per_step = 5 + (c->F > 0 ? 5 : 0) + (c->NW > 0 ? 1 : 0);
+    });
+}
+
+void ugks_destroy(ugks_case *c)
+{
+    if (!c) return;
+    for (auto e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->release();
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,1100 @@
+// ugks_kernels.cu -- the CUDA kernels of one UGKS time step (sm_103a).
+//
+// One step (Algorithm 1 of arXiv:2412.06546, reorganised for the GPU):
+//   k_prep        cell records from W^n, q^n; far-field ghost states     (Alg.1 l.1, Sec. 2.5)
+//   k_macro_grad  limited least-squares gradient of W                    (Alg.1 l.2)
+//   k_face_pre    face states W_L, W_R, interface macro gradient, q0     (Alg.1 l.3)
+//   k_face_sum1   half-range moments over the velocity grid -> W0        (Sec. 2.4)
+//   k_face_fin1   g0 parameters, tau0, time integrals q1..q5             (Sec. 2.4)
+//   k_face_sum2   moments of g0 for the slope systems                    (Sec. 2.4)
+//   k_face_fin2   spatial and time slopes of g0                          (Sec. 2.4)
+//   k_wall_sum    wall density from zero net mass flux                   (Eq. maxWalldes)
+//   k_gather      per (cell patch, velocity tile): micro slopes, face fluxes, stage 1,
+//                 moments of the flux residual                           (Alg.1 l.4-10, Eq. microS1)
+//   k_update_W    W^{n+1} and stage-2 coefficients                       (Eq. macroscopicUpdata)
+//   k_collide     stage 2 and the heat flux of f^{n+1}                   (Eq. microS2)
+// All per-velocity arithmetic is in T (double or float); moment sums are
+// reduced per warp and promoted to FP64; macroscopic scalars are FP64.
+#include "ugks_device.cuh"
+#include "ugks_kernels.h"
+
+#include <cmath>
+
+namespace ugks {
+
+// ------------------------------------------------------------ FP64 helpers
+struct Prim {
+    double rho, U[MAXD], lam, T;
+};
+
+__device__ __forceinline__ Prim prim_of(const double *W, int D)
+{
+    Prim p;
+    p.rho = W[0];
+    double ke = 0.0;
+    for (int d = 0; d < MAXD; ++d) p.U[d] = 0.0;
+    for (int d = 0; d < D; ++d) {
+        p.U[d] = W[1 + d] / W[0];
+        ke += p.U[d] * p.U[d];
+    }
+    double E = W[D + 1] / W[0];
+    p.T = (2.0 / 3.0) * (E - 0.5 * ke);
+    p.lam = 1.0 / (2.0 * p.T);
+    return p;
+}
+
+__device__ __forceinline__ double pref_of(double rho, double lam, int D)
+{
+    double a = lam / 3.141592653589793238462643383279502884;
+    return D == 2 ? rho * a : rho * a * sqrt(a);
+}
+
+// collision time tau = mu_ref T^omega / (rho T)  (VHS viscosity, p = rho T)
+template <typename T>
+__device__ __forceinline__ double tau_of(const DevCase<T> &dc, double rho, double Tmp)
+{
+    return dc.mu_ref * pow(Tmp, dc.omega) / (rho * Tmp);
+}
+
+// Time integrals of c1..c5 over [0, dt] (Sec. 2.4), written with x = dt/tau,
+// E = 1 - e^{-x}:  q1 = dt E/x, q2 = dt^2 (x e^{-x} - E)/x^2, q3 = dt (x - E)/x,
+// q4 = dt^2 (2E - x(1 + e^{-x}))/x^2, q5 = dt^2 (x^2/2 - x + E)/x^2.
+// Below x = 1/2 each bracket is summed from its Taylor series.
+__device__ void time_integrals(double dt, double tau, double q[5])
+{
+    const double x = dt / tau;
+    if (x < 0.5) {
+        double s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
+        double xp = 1.0;       // x^{j-2} for j >= 2
+        double inv_fact = 1.0; // 1/j!
+        double xm1 = 1.0;      // x^{j-1}
+        for (int j = 1; j <= 22; ++j) {
+            inv_fact /= (double)j;
+            const double sg = (j & 1) ? 1.0 : -1.0;   // (-1)^{j+1}
+            s1 += sg * xm1 * inv_fact;                  // E/x
+            if (j >= 2) {
+                const double xm2 = xp;                  // x^{j-2}
+                s2 += sg * (1.0 - (double)j) * xm2 * inv_fact;   // (E - x e)/x^2
+                s3 += -sg * xm1 * inv_fact;                      // (x - E)/x
+                if (j >= 3) {
+                    s4 += sg * (2.0 - (double)j) * xm2 * inv_fact;   // (2E - x(1+e))/x^2
+                    s5 += sg * xm2 * inv_fact;                        // (x^2/2 - x + E)/x^2
+                }
+                xp *= x;
+            }
+            xm1 *= x;
+        }
+        q[0] = dt * s1;
+        q[1] = -dt * dt * s2;
+        q[2] = dt * s3;
+        q[3] = dt * dt * s4;
+        q[4] = dt * dt * s5;
+    } else {
+        const double e = exp(-x);
+        const double E = -expm1(-x);
+        const double ix = 1.0 / x, ix2 = ix * ix;
+        q[0] = dt * E * ix;
+        q[1] = dt * dt * (x * e - E) * ix2;
+        q[2] = dt * (x - E) * ix;
+        q[3] = dt * dt * (2.0 * E - x * (1.0 + e)) * ix2;
+        q[4] = dt * dt * (0.5 * x * x - x + E) * ix2;
+    }
+}
+
+// Venkatakrishnan factor on FP64 data (macro reconstruction)
+__device__ __forceinline__ double venkat_d(double d1, double d2, double e2)
+{
+    double a2 = d1 * d1 + e2;
+    double num = a2 + 2.0 * d1 * d2;
+    double den = a2 + d2 * (2.0 * d2 + d1);
+    return den > 0.0 ? num / den : 1.0;
+}
+
+// ------------------------------------------------------------ init / moments
+template <typename T, int D, int NC>
+__global__ void k_init_f(DevCase<T> dc)
+{
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= dc.C) return;
+    Prim p = prim_of(dc.W + (size_t)c * (D + 2), D);
+    T rec[GREC];
+    for (int d = 0; d < 3; ++d) rec[GR_U + d] = (T)p.U[d];
+    rec[GR_LAM] = (T)p.lam;
+    rec[GR_PREF] = (T)pref_of(p.rho, p.lam, D);
+    rec[GR_NB] = (T)(dc.nxi / (2.0 * p.lam));
+    const size_t rs = (size_t)NC * dc.nvp;
+    for (int k = lane; k < dc.nvp; k += 32) {
+        T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
+        T H = maxwell_h<T, D>(rec, u);
+        dc.f_cur[(size_t)c * rs + k] = H;
+        if (NC == 2) dc.f_cur[(size_t)c * rs + dc.nvp + k] = rec[GR_NB] * H;
+    }
+}
+
+// heat flux q = 1/2 sum_k w c (|c|^2 h + b), c = u - U(W)  (Sec. 2.1)
+template <typename T, int D, int NC>
+__global__ void k_heatflux(DevCase<T> dc)
+{
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= dc.C) return;
+    Prim p = prim_of(dc.W + (size_t)c * (D + 2), D);
+    T U[3] = {(T)p.U[0], (T)p.U[1], (T)p.U[2]};
+    const size_t rs = (size_t)NC * dc.nvp;
+    T acc[D];
+    for (int d = 0; d < D; ++d) acc[d] = 0;
+    for (int k = lane; k < dc.nvp; k += 32) {
+        T cc[D], c2 = 0;
+        for (int d = 0; d < D; ++d) {
+            cc[d] = dc.u[d][k] - U[d];
+            c2 += cc[d] * cc[d];
+        }
+        T h = dc.f_cur[(size_t)c * rs + k];
+        T e = c2 * h + (NC == 2 ? dc.f_cur[(size_t)c * rs + dc.nvp + k] : T(0));
+        T we = dc.w[k] * e;
+        for (int d = 0; d < D; ++d) acc[d] += cc[d] * we;
+    }
+    for (int d = 0; d < D; ++d) {
+        T s = warp_sum(acc[d]);
+        if (lane == 0) dc.q[(size_t)c * D + d] = 0.5 * (double)s;
+    }
+}
+
+// ------------------------------------------------------------ k_prep
+template <typename T, int D, int NC>
+__global__ void k_prep(DevCase<T> dc)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int M = D + 2;
+    if (t < dc.C) {
+        const int c = t;
+        Prim p = prim_of(dc.W + (size_t)c * M, D);
+        if (!(p.rho > 0.0) || !(p.T > 0.0)) atomicOr(dc.flags, 1);
+        double tau = tau_of(dc, p.rho, p.T);
+        double kappa = 4.0 * (1.0 - dc.Pr) * p.lam * p.lam / (5.0 * p.rho);
+        T *r = dc.crec + (size_t)c * CREC;
+        for (int d = 0; d < 3; ++d) r[CR_U + d] = (T)p.U[d];
+        r[CR_LAM] = (T)p.lam;
+        r[CR_PREF] = (T)pref_of(p.rho, p.lam, D);
+        for (int d = 0; d < 3; ++d) r[CR_KQ + d] = d < D ? (T)(kappa * dc.q[(size_t)c * D + d]) : T(0);
+        r[CR_C] = (T)(0.5 * dc.dt / tau);
+        r[CR_NB] = (T)(dc.nxi / (2.0 * p.lam));
+        return;
+    }
+    const int g = t - dc.C;
+    if (g >= dc.G) return;
+    // far-field ghost (Sec. 2.5): free stream where it enters (U_inf . n < 0),
+    // zero-gradient extrapolation of the cell state elsewhere
+    const int f = dc.gface[g];
+    const int own = dc.fL[f];
+    double un = __dmul_rn(dc.inf_W[1] / dc.inf_W[0], dc.fn_d[(size_t)f * D]);
+    un = __dadd_rn(un, __dmul_rn(dc.inf_W[2] / dc.inf_W[0], dc.fn_d[(size_t)f * D + 1]));
+    if (D == 3) un = __dadd_rn(un, __dmul_rn(dc.inf_W[3] / dc.inf_W[0], dc.fn_d[(size_t)f * D + 2]));
+    double *Wg = dc.Wg + (size_t)g * M;
+    for (int m = 0; m < M; ++m) Wg[m] = un < 0.0 ? dc.inf_W[m] : dc.W[(size_t)own * M + m];
+    Prim p = prim_of(Wg, D);
+    T *r = dc.grec + (size_t)g * GREC;
+    for (int d = 0; d < 3; ++d) r[GR_U + d] = (T)p.U[d];
+    r[GR_LAM] = (T)p.lam;
+    r[GR_PREF] = (T)pref_of(p.rho, p.lam, D);
+    r[GR_NB] = (T)(dc.nxi / (2.0 * p.lam));
+}
+
+// ------------------------------------------------------------ k_macro_grad
+template <typename T, int D, int NC>
+__global__ void k_macro_grad(DevCase<T> dc)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int M = D + 2;
+    if (c >= dc.C) return;
+    const double *Wc = dc.W + (size_t)c * M;
+    const int q0 = dc.nb_ptr[c], q1 = dc.nb_ptr[c + 1];
+    const int s0 = dc.cf_ptr[c], s1 = dc.cf_ptr[c + 1];
+    const double e2 = dc.eps2_d[c];
+    for (int m = 0; m < M; ++m) {
+        const double vi = Wc[m];
+        double g[D], vmax = vi, vmin = vi;
+        for (int d = 0; d < D; ++d) g[d] = 0.0;
+        for (int q = q0; q < q1; ++q) {
+            const int id = dc.nb_id[q];
+            const double vj = id >= 0 ? dc.W[(size_t)id * M + m] : dc.Wg[(size_t)(-id - 1) * M + m];
+            for (int d = 0; d < D; ++d) g[d] += dc.nb_a_d[(size_t)q * D + d] * (vj - vi);
+            vmax = fmax(vmax, vj);
+            vmin = fmin(vmin, vj);
+        }
+        if (dc.limiter) {
+            double phi = 1.0;
+            for (int s = s0; s < s1; ++s) {
+                double d2 = 0.0;
+                for (int d = 0; d < D; ++d) d2 += g[d] * dc.cf_r_d[(size_t)s * D + d];
+                double d1 = d2 > 0.0 ? vmax - vi : vmin - vi;
+                phi = fmin(phi, venkat_d(d1, d2, e2));
+            }
+            for (int d = 0; d < D; ++d) g[d] *= phi;
+        }
+        for (int d = 0; d < D; ++d) dc.gradW[((size_t)c * D + d) * M + m] = g[d];
+    }
+}
+
+// ------------------------------------------------------------ face pass
+// face state W_c + gradW_c . r, falling back to W_c if rho or the thermal
+// energy would not be positive
+template <int D>
+__device__ __forceinline__ void face_state(const double *W, const double *gradW, int c, const double *r,
+                                           double *Ws)
+{
+    constexpr int M = D + 2;
+    for (int m = 0; m < M; ++m) {
+        double s = W[(size_t)c * M + m];
+        for (int d = 0; d < D; ++d) s += gradW[((size_t)c * D + d) * M + m] * r[d];
+        Ws[m] = s;
+    }
+    double ke = 0.0;
+    for (int d = 0; d < D; ++d) ke += Ws[1 + d] * Ws[1 + d];
+    if (!(Ws[0] > 0.0) || !(Ws[D + 1] - 0.5 * ke / Ws[0] > 0.0))
+        for (int m = 0; m < M; ++m) Ws[m] = W[(size_t)c * M + m];
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void side_record(const double *Ws, double nxi, T *rec)
+{
+    Prim p = prim_of(Ws, D);
+    for (int d = 0; d < 3; ++d) rec[GR_U + d] = (T)p.U[d];
+    rec[GR_LAM] = (T)p.lam;
+    rec[GR_PREF] = (T)pref_of(p.rho, p.lam, D);
+    rec[GR_NB] = (T)(nxi / (2.0 * p.lam));
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_pre(DevCase<T> dc)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int M = D + 2;
+    if (f >= dc.F) return;
+    const int typ = dc.ftype[f];
+    if (typ == FT_WALL) return;
+    const int L = dc.fL[f];
+    double WL[M], WR[M], rL[D], rR[D];
+    for (int d = 0; d < D; ++d) rL[d] = dc.frL_d[(size_t)f * D + d];
+    face_state<D>(dc.W, dc.gradW, L, rL, WL);
+    double *dW0 = dc.fdW0 + (size_t)f * D * M;
+    double *q0 = dc.fq0 + (size_t)f * D;
+    if (typ == FT_FARFIELD) {
+        const int g = dc.faux[f];
+        for (int m = 0; m < M; ++m) WR[m] = dc.Wg[(size_t)g * M + m];
+        for (int d = 0; d < D; ++d) {
+            for (int m = 0; m < M; ++m) dW0[d * M + m] = 0.5 * dc.gradW[((size_t)L * D + d) * M + m];
+            q0[d] = 0.5 * dc.q[(size_t)L * D + d];
+        }
+    } else {
+        const int R = dc.fR[f];
+        for (int d = 0; d < D; ++d) rR[d] = dc.frR_d[(size_t)f * D + d];
+        face_state<D>(dc.W, dc.gradW, R, rR, WR);
+        for (int d = 0; d < D; ++d) {
+            for (int m = 0; m < M; ++m)
+                dW0[d * M + m] = 0.5 * (dc.gradW[((size_t)L * D + d) * M + m] + dc.gradW[((size_t)R * D + d) * M + m]);
+            q0[d] = 0.5 * (dc.q[(size_t)L * D + d] + dc.q[(size_t)R * D + d]);
+        }
+    }
+    side_record<T, D>(WL, dc.nxi, dc.fside + (size_t)f * 2 * GREC);
+    side_record<T, D>(WR, dc.nxi, dc.fside + (size_t)f * 2 * GREC + GREC);
+    Prim pL = prim_of(WL, D), pR = prim_of(WR, D);
+    for (int d = 0; d < D; ++d) dc.fUref[(size_t)f * D + d] = 0.5 * (pL.U[d] + pR.U[d]);
+}
+
+// half-range moments: sum_k w psi_c [H(u_n) g_L + (1 - H(u_n)) g_R], centred at U_ref
+template <typename T, int D, int NC>
+__global__ void k_face_sum1(DevCase<T> dc)
+{
+    const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    constexpr int M = D + 2;
+    if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
+    const T *sL = dc.fside + (size_t)f * 2 * GREC;
+    const T *sR = sL + GREC;
+    T n[D], Ur[D];
+    for (int d = 0; d < D; ++d) {
+        n[d] = dc.fn[(size_t)f * D + d];
+        Ur[d] = (T)dc.fUref[(size_t)f * D + d];
+    }
+    T acc[M];
+    for (int m = 0; m < M; ++m) acc[m] = 0;
+    for (int k = lane; k < dc.nvp; k += 32) {
+        T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
+        T un = normal_velocity<T, D>(u, n);
+        T h, b;
+        if (un != T(0)) {
+            const T *s = un > T(0) ? sL : sR;
+            h = maxwell_h<T, D>(s, u);
+            b = s[GR_NB] * h;
+        } else {
+            T hl = maxwell_h<T, D>(sL, u), hr = maxwell_h<T, D>(sR, u);
+            h = T(0.5) * hl + T(0.5) * hr;
+            b = T(0.5) * sL[GR_NB] * hl + T(0.5) * sR[GR_NB] * hr;
+        }
+        T wk = dc.w[k];
+        T c2 = 0;
+        T wh = wk * h;
+        acc[0] += wh;
+        for (int d = 0; d < D; ++d) {
+            T c = u[d] - Ur[d];
+            c2 += c * c;
+            acc[1 + d] += c * wh;
+        }
+        acc[D + 1] += T(0.5) * wk * (c2 * h + b);
+    }
+    for (int m = 0; m < M; ++m) {
+        T s = warp_sum(acc[m]);
+        if (lane == 0) dc.fsum1[(size_t)f * M + m] = (double)s;
+    }
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_fin1(DevCase<T> dc)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int M = D + 2;
+    if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
+    const double *S = dc.fsum1 + (size_t)f * M;
+    const double *Ur = dc.fUref + (size_t)f * D;
+    // shift the centred sums back: psi = L psi_c with c = u - U_ref
+    double W0[M];
+    W0[0] = S[0];
+    double uS = 0.0, uu = 0.0;
+    for (int d = 0; d < D; ++d) {
+        W0[1 + d] = S[1 + d] + Ur[d] * S[0];
+        uS += Ur[d] * S[1 + d];
+        uu += Ur[d] * Ur[d];
+    }
+    W0[D + 1] = S[D + 1] + uS + 0.5 * uu * S[0];
+    Prim p = prim_of(W0, D);
+    double *pp = dc.fprim0 + (size_t)f * M;
+    pp[0] = p.rho;
+    for (int d = 0; d < D; ++d) pp[1 + d] = p.U[d];
+    pp[D + 1] = p.lam;
+    T *r = dc.frec + (size_t)f * FREC;
+    for (int d = 0; d < 3; ++d) r[FR_U + d] = (T)p.U[d];
+    r[FR_LAM] = (T)p.lam;
+    r[FR_PREF] = (T)pref_of(p.rho, p.lam, D);
+    const double kappa = 4.0 * (1.0 - dc.Pr) * p.lam * p.lam / (5.0 * p.rho);
+    for (int d = 0; d < 3; ++d) r[FR_KQ + d] = d < D ? (T)(kappa * dc.fq0[(size_t)f * D + d]) : T(0);
+    double qs[5];
+    time_integrals(dc.dt, tau_of(dc, p.rho, p.T), qs);
+    for (int i = 0; i < 5; ++i) r[FR_QS + i] = (T)qs[i];
+    r[FR_NB] = (T)(dc.nxi / (2.0 * p.lam));
+    r[FR_XB] = (T)(dc.nxi * (dc.nxi + 2.0) / (4.0 * p.lam * p.lam));
+}
+
+// number of unique entries of a symmetric (D+2)x(D+2) matrix
+template <int D> struct Sym { static constexpr int N = (D + 2) * (D + 3) / 2; };
+
+// unique entries of P_c(c) = int psi_c psi_c^T g0 dxi / H0, row-major upper triangle
+template <typename T, int D>
+__device__ __forceinline__ void psi_c_outer(const T c[D], T c2, T nb, T xb, T P[Sym<D>::N])
+{
+    constexpr int M = D + 2;
+    const T e = T(0.5) * (c2 + nb);                               // int psi_E g / H
+    const T ee = T(0.25) * (c2 * c2 + T(2) * nb * c2 + xb);       // int psi_E^2 g / H
+    T v[M];
+    v[0] = T(1);
+    for (int d = 0; d < D; ++d) v[1 + d] = c[d];
+    int t = 0;
+    for (int i = 0; i < M; ++i)
+        for (int j = i; j < M; ++j) {
+            T val;
+            if (j < M - 1) val = v[i] * v[j];
+            else if (i < M - 1) val = v[i] * e;
+            else val = ee;
+            P[t++] = val;
+        }
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_sum2(DevCase<T> dc)
+{
+    const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    constexpr int NS = Sym<D>::N;
+    constexpr int S2 = NS * (D + 1);
+    if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
+    const T *fr = dc.frec + (size_t)f * FREC;
+    T U0[D];
+    for (int d = 0; d < D; ++d) U0[d] = fr[FR_U + d];
+    const T lam = fr[FR_LAM], pref = fr[FR_PREF], nb = fr[FR_NB], xb = fr[FR_XB];
+    T acc[S2];
+    for (int i = 0; i < S2; ++i) acc[i] = 0;
+    for (int k = lane; k < dc.nvp; k += 32) {
+        T c[D], c2 = 0;
+        for (int d = 0; d < D; ++d) {
+            c[d] = dc.u[d][k] - U0[d];
+            c2 += c[d] * c[d];
+        }
+        const T wH = dc.w[k] * pref * dexp(-lam * c2);
+        T P[NS];
+        psi_c_outer<T, D>(c, c2, nb, xb, P);
+        for (int i = 0; i < NS; ++i) {
+            const T v = wH * P[i];
+            acc[i] += v;
+            for (int d = 0; d < D; ++d) acc[NS * (1 + d) + i] += c[d] * v;
+        }
+    }
+    for (int i = 0; i < S2; ++i) {
+        T s = warp_sum(acc[i]);
+        if (lane == 0) dc.fsum2[(size_t)f * S2 + i] = (double)s;
+    }
+}
+
+// Cholesky solve of the SPD system A x = b (n <= 5), A overwritten
+__device__ void chol_solve(int n, double *A, double *b, int nrhs, int ldb)
+{
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+        const double Ljj = sqrt(s);
+        A[j * n + j] = Ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = t / Ljj;
+        }
+    }
+    for (int r = 0; r < nrhs; ++r) {
+        double *x = b + r * ldb;
+        for (int i = 0; i < n; ++i) {
+            double t = x[i];
+            for (int k = 0; k < i; ++k) t -= A[i * n + k] * x[k];
+            x[i] = t / A[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double t = x[i];
+            for (int k = i + 1; k < n; ++k) t -= A[k * n + i] * x[k];
+            x[i] = t / A[i * n + i];
+        }
+    }
+}
+
+// slopes of g0 in the centred basis: M0 = L Mc L^T, sum_k w u_d psi psi^T g0 =
+// L (Tc_d + U0_d Mc) L^T with psi = L psi_c.  Then beta_d = L^T a_d solves
+// Mc beta_d = L^{-1} dW0/dx_d, and the compatibility condition gives
+// beta_A = L^T A = -Mc^{-1} sum_d Tc_d beta_d - sum_d U0_d beta_d.
+template <typename T, int D, int NC>
+__global__ void k_face_fin2(DevCase<T> dc)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int M = D + 2, NS = Sym<D>::N, S2 = NS * (D + 1);
+    if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
+    const double *S = dc.fsum2 + (size_t)f * S2;
+    double Mc[M * M], Tc[D][M * M];
+    {
+        int t = 0;
+        for (int i = 0; i < M; ++i)
+            for (int j = i; j < M; ++j) {
+                Mc[i * M + j] = Mc[j * M + i] = S[t];
+                for (int d = 0; d < D; ++d) Tc[d][i * M + j] = Tc[d][j * M + i] = S[NS * (1 + d) + t];
+                ++t;
+            }
+    }
+    const double *pp = dc.fprim0 + (size_t)f * M;
+    double U0[D], uu = 0.0;
+    for (int d = 0; d < D; ++d) {
+        U0[d] = pp[1 + d];
+        uu += U0[d] * U0[d];
+    }
+    // right-hand sides L^{-1} dW0_d
+    double B[(D + 1) * M];
+    const double *dW = dc.fdW0 + (size_t)f * D * M;
+    for (int d = 0; d < D; ++d) {
+        const double *g = dW + d * M;
+        double *x = B + d * M;
+        x[0] = g[0];
+        double um = 0.0;
+        for (int e = 0; e < D; ++e) {
+            x[1 + e] = g[1 + e] - U0[e] * g[0];
+            um += U0[e] * g[1 + e];
+        }
+        x[D + 1] = g[D + 1] - um + 0.5 * uu * g[0];
+    }
+    double A[M * M];
+    for (int i = 0; i < M * M; ++i) A[i] = Mc[i];
+    chol_solve(M, A, B, D, M);              // B[d] = beta_d ; A holds the factor
+    double *xa = B + D * M;
+    for (int i = 0; i < M; ++i) {
+        double s = 0.0;
+        for (int d = 0; d < D; ++d)
+            for (int j = 0; j < M; ++j) s += Tc[d][i * M + j] * B[d * M + j];
+        xa[i] = -s;
+    }
+    // solve with the stored factor
+    for (int i = 0; i < M; ++i) {
+        double t = xa[i];
+        for (int k = 0; k < i; ++k) t -= A[i * M + k] * xa[k];
+        xa[i] = t / A[i * M + i];
+    }
+    for (int i = M - 1; i >= 0; --i) {
+        double t = xa[i];
+        for (int k = i + 1; k < M; ++k) t -= A[k * M + i] * xa[k];
+        xa[i] = t / A[i * M + i];
+    }
+    for (int i = 0; i < M; ++i)
+        for (int d = 0; d < D; ++d) xa[i] -= U0[d] * B[d * M + i];
+    T *r = dc.frec + (size_t)f * FREC;
+    for (int i = 0; i < (D + 1) * M; ++i) r[FR_BETA + i] = (T)B[i];
+}
+
+// ------------------------------------------------------------ walls
+// rho_w from zero net mass flux (Eq. maxWalldes): outgoing particles (u_n > 0)
+// carry the interior reconstruction transported freely over the step,
+// incoming ones the wall Maxwellian.
+template <typename T, int D, int NC>
+__global__ void k_wall_sum(DevCase<T> dc)
+{
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (s >= dc.NW) return;
+    const int f = dc.wface[s];
+    const int c = dc.fL[f];
+    const int tag = dc.ftag[f];
+    const double Tw = dc.wallT[tag];
+    const double lw = 1.0 / (2.0 * Tw);
+    T wr[GREC];
+    for (int d = 0; d < 3; ++d) wr[GR_U + d] = (T)dc.wallU[tag * 3 + d];
+    wr[GR_LAM] = (T)lw;
+    wr[GR_PREF] = (T)pref_of(1.0, lw, D);
+    wr[GR_NB] = (T)(dc.nxi / (2.0 * lw));
+    T n[D], r[D];
+    for (int d = 0; d < D; ++d) {
+        n[d] = dc.fn[(size_t)f * D + d];
+        r[d] = (T)dc.frL_d[(size_t)f * D + d];
+    }
+    const T hdt = T(0.5 * dc.dt);
+    const size_t rs = (size_t)NC * dc.nvp;
+    T num = 0, den = 0;
+    for (int k = lane; k < dc.nvp; k += 32) {
+        T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
+        T un = normal_velocity<T, D>(u, n);
+        if (un > T(0)) {
+            T g[NC][D];
+            cell_slope<T, D, NC>(dc, dc.f_cur, c, k, u, g);
+            T hin = dc.f_cur[(size_t)c * rs + k], ug = 0;
+            for (int d = 0; d < D; ++d) {
+                hin += g[0][d] * r[d];
+                ug += u[d] * g[0][d];
+            }
+            num += dc.w[k] * un * (hin - hdt * ug);
+        } else if (un < T(0)) {
+            den += dc.w[k] * un * maxwell_h<T, D>(wr, u);
+        }
+    }
+    num = warp_sum(num);
+    den = warp_sum(den);
+    if (lane == 0) {
+        const double rw = -(double)num / (double)den;
+        dc.rho_w[s] = rw;
+        T *w = dc.wrec + (size_t)s * GREC;
+        for (int i = 0; i < GREC; ++i) w[i] = wr[i];
+        w[GR_PREF] = (T)pref_of(rw, lw, D);
+    }
+}
+
+// ------------------------------------------------------------ gather pass
+// One CTA per (patch of P consecutive cells, tile of V = 32*TV velocities).
+// Phase A: limited slopes of the patch cells and their face neighbours (ring)
+//          into shared memory, each computed once.
+// Phase B: per patch cell, the flux of every face (Eq. microscopicFlux with
+//          Eq. fullSolution; walls per Sec. 2.5), stage 1 (Eq. microS1) written
+//          to f_nxt, and the moments sum_k w psi_k R_k of the flux residual for
+//          the W update (Eq. macroscopicUpdata / macroscopicFlux).
+template <typename T, int D, int NC, int TV>
+__global__ void __launch_bounds__(256) k_gather(DevCase<T> dc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sg = reinterpret_cast<T *>(smem_raw);
+    constexpr int V = 32 * TV;
+    constexpr int M = D + 2;
+    const int p = blockIdx.x, vt = blockIdx.y, k0 = vt * V;
+    const int cb = p * dc.P;
+    const int npc = min(dc.P, dc.C - cb);
+    const int rb = dc.ring_ptr[p], re = dc.ring_ptr[p + 1];
+    const int nslope = npc + (re - rb);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const T *__restrict__ f = dc.f_cur;
+    const size_t rs = (size_t)NC * dc.nvp;
+
+    T u[TV][3];
+#pragma unroll
+    for (int j = 0; j < TV; ++j) {
+        const int k = k0 + lane + 32 * j;
+        u[j][0] = dc.u[0][k];
+        u[j][1] = dc.u[1][k];
+        u[j][2] = D == 3 ? dc.u[2][k] : T(0);
+    }
+
+    // ---- phase A: slopes (Alg. 1 line 5)
+    for (int s = warp; s < nslope; s += nwarps) {
+        const int c = s < npc ? cb + s : dc.ring_cells[rb + s - npc];
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+            T g[NC][D];
+            cell_slope<T, D, NC>(dc, f, c, k0 + lane + 32 * j, u[j], g);
+#pragma unroll
+            for (int m = 0; m < NC; ++m)
+#pragma unroll
+                for (int d = 0; d < D; ++d) sg[((s * NC + m) * D + d) * V + lane + 32 * j] = g[m][d];
+        }
+    }
+    __syncthreads();
+
+    // ---- phase B: fluxes, stage 1, moments (Alg. 1 lines 6-8, 10)
+    const T dt = (T)dc.dt;
+    const T hdt2 = T(0.5 * dc.dt * dc.dt);
+    for (int s = warp; s < npc; s += nwarps) {
+        const int c = cb + s;
+        T R[TV][NC];
+#pragma unroll
+        for (int j = 0; j < TV; ++j)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) R[j][m] = 0;
+        const int e0 = dc.cf_ptr[c], e1 = dc.cf_ptr[c + 1];
+        for (int e = e0; e < e1; ++e) {
+            const int fid = dc.cf_face[e];
+            const T coef = dc.cf_coef[e];
+            const int typ = dc.ftype[fid];
+            T n[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) n[d] = dc.fn[(size_t)fid * D + d];
+            if (typ == FT_WALL) {
+                const T *wr = dc.wrec + (size_t)dc.faux[fid] * GREC;
+                const int sl = dc.cf_sL[e];
+                T r[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) r[d] = dc.cf_r[(size_t)e * D + d];
+#pragma unroll
+                for (int j = 0; j < TV; ++j) {
+                    const int k = k0 + lane + 32 * j;
+                    const T un = normal_velocity<T, D>(u[j], n);
+                    T F[NC];
+                    if (un > T(0)) {
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            T fin = f[(size_t)c * rs + (size_t)m * dc.nvp + k], ug = 0;
+#pragma unroll
+                            for (int d = 0; d < D; ++d) {
+                                const T gd = sg[((sl * NC + m) * D + d) * V + lane + 32 * j];
+                                fin += gd * r[d];
+                                ug += u[j][d] * gd;
+                            }
+                            F[m] = un * (dt * fin - hdt2 * ug);
+                        }
+                    } else {
+                        const T H = maxwell_h<T, D>(wr, u[j]);
+                        F[0] = un * dt * H;
+                        if (NC == 2) F[NC - 1] = un * dt * wr[GR_NB] * H;
+                    }
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) R[j][m] += coef * F[m];
+                }
+            } else {
+                const T *fr = dc.frec + (size_t)fid * FREC;
+                const int sL = dc.cf_sL[e], sR = dc.cf_sR[e];
+                const int cL = dc.fL[fid], cR = dc.fR[fid];
+                T rL[D], rR[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    rL[d] = (T)dc.frL_d[(size_t)fid * D + d];
+                    rR[d] = typ == FT_FARFIELD ? T(0) : (T)dc.frR_d[(size_t)fid * D + d];
+                }
+#pragma unroll
+                for (int j = 0; j < TV; ++j) {
+                    const int k = k0 + lane + 32 * j;
+                    const T un = normal_velocity<T, D>(u[j], n);
+                    T fup[NC], ugf[NC];
+                    const bool left = un > T(0);
+                    if (!left && typ == FT_FARFIELD) {
+                        const T *gr = dc.grec + (size_t)dc.faux[fid] * GREC;
+                        const T H = maxwell_h<T, D>(gr, u[j]);
+                        fup[0] = H;
+                        if (NC == 2) fup[NC - 1] = gr[GR_NB] * H;
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) ugf[m] = 0;
+                    } else {
+                        const int slot = left ? sL : sR;
+                        const int cu = left ? cL : cR;
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            T v = f[(size_t)cu * rs + (size_t)m * dc.nvp + k], ug = 0;
+#pragma unroll
+                            for (int d = 0; d < D; ++d) {
+                                const T gd = sg[((slot * NC + m) * D + d) * V + lane + 32 * j];
+                                v += gd * (left ? rL[d] : rR[d]);
+                                ug += u[j][d] * gd;
+                            }
+                            fup[m] = v;
+                            ugf[m] = ug;
+                        }
+                    }
+                    T F[NC];
+                    interface_flux<T, D, NC>(fr, u[j], un, fup, ugf, F);
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) R[j][m] += coef * F[m];
+                }
+            }
+        }
+        // stage 1 and the moments of R
+        const T *cr = dc.crec + (size_t)c * CREC;
+        const T cc = cr[CR_C];
+        T mom[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) mom[i] = 0;
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+            const int k = k0 + lane + 32 * j;
+            T fp[NC];
+            shakhov_fplus<T, D, NC>(cr, u[j], fp);
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                const size_t o = (size_t)c * rs + (size_t)m * dc.nvp + k;
+                const T fc = f[o];
+                dc.f_nxt[o] = fc + R[j][m] + cc * (fp[m] - fc);
+            }
+            const T wk = dc.w[k];
+            T u2 = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) u2 += u[j][d] * u[j][d];
+            const T wr0 = wk * R[j][0];
+            mom[0] += wr0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) mom[1 + d] += u[j][d] * wr0;
+            mom[D + 1] += T(0.5) * (u2 * wr0 + (NC == 2 ? wk * R[j][NC - 1] : T(0)));
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const T sm = warp_sum(mom[i]);
+            if (lane == 0) dc.dW_part[((size_t)c * dc.n_vt + vt) * M + i] = (double)sm;
+        }
+    }
+}
+
+// ------------------------------------------------------------ W update
+template <typename T, int D, int NC>
+__global__ void __launch_bounds__(256) k_update_W(DevCase<T> dc)
+{
+    constexpr int M = D + 2;
+    __shared__ double red[2 * M][8];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double dsq[M], wsq[M];
+    for (int m = 0; m < M; ++m) dsq[m] = wsq[m] = 0.0;
+    if (c < dc.C) {
+        double *Wc = dc.W + (size_t)c * M;
+        for (int m = 0; m < M; ++m) {
+            double s = 0.0;
+            for (int t = 0; t < dc.n_vt; ++t) s += dc.dW_part[((size_t)c * dc.n_vt + t) * M + m];
+            wsq[m] = Wc[m] * Wc[m];
+            dsq[m] = s * s;
+            Wc[m] += s;
+        }
+        Prim p = prim_of(Wc, D);
+        if (!(p.rho > 0.0) || !(p.T > 0.0) || !isfinite(p.rho) || !isfinite(p.T)) atomicOr(dc.flags, 1);
+        const double tau = tau_of(dc, p.rho, p.T);
+        const double kappa = 4.0 * (1.0 - dc.Pr) * p.lam * p.lam / (5.0 * p.rho);
+        T *r = dc.krec + (size_t)c * CREC;
+        for (int d = 0; d < 3; ++d) r[CR_U + d] = (T)p.U[d];
+        r[CR_LAM] = (T)p.lam;
+        r[CR_PREF] = (T)pref_of(p.rho, p.lam, D);
+        for (int d = 0; d < 3; ++d) r[CR_KQ + d] = d < D ? (T)(kappa * dc.q[(size_t)c * D + d]) : T(0);
+        r[CR_C] = (T)(0.5 * dc.dt / tau);
+        r[CR_NB] = (T)(dc.nxi / (2.0 * p.lam));
+    }
+    // deterministic block partials of the residual
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int m = 0; m < M; ++m) {
+        double a = warp_sum(dsq[m]), b = warp_sum(wsq[m]);
+        if (lane == 0) {
+            red[m][warp] = a;
+            red[M + m][warp] = b;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * M) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
+        dc.res_part[(size_t)blockIdx.x * 2 * M + threadIdx.x] = s;
+    }
+}
+
+template <int M>
+__global__ void k_residual(const double *res_part, int nblocks, double *res)
+{
+    __shared__ double acc[2 * M][32];
+    const int t = threadIdx.x;
+    for (int i = 0; i < 2 * M; ++i) {
+        double s = 0.0;
+        for (int b = t; b < nblocks; b += 32) s += res_part[(size_t)b * 2 * M + i];
+        acc[i][t] = s;
+    }
+    __syncwarp();
+    if (t < M) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < 32; ++w) {
+            a += acc[t][w];
+            b += acc[M + t][w];
+        }
+        res[t] = b > 0.0 ? sqrt(a) / sqrt(b) : sqrt(a);
+    }
+}
+
+// ------------------------------------------------------------ stage 2
+template <typename T, int D, int NC>
+__global__ void k_collide(DevCase<T> dc)
+{
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= dc.C) return;
+    const T *kr = dc.krec + (size_t)c * CREC;
+    const T cc = kr[CR_C];
+    const T inv = T(1) / (T(1) + cc);
+    T U[D];
+    for (int d = 0; d < D; ++d) U[d] = kr[CR_U + d];
+    const size_t rs = (size_t)NC * dc.nvp;
+    T acc[D];
+    for (int d = 0; d < D; ++d) acc[d] = 0;
+    for (int k = lane; k < dc.nvp; k += 32) {
+        T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
+        T fp[NC];
+        shakhov_fplus<T, D, NC>(kr, u, fp);
+        T fn[NC];
+        for (int m = 0; m < NC; ++m) {
+            const size_t o = (size_t)c * rs + (size_t)m * dc.nvp + k;
+            fn[m] = (dc.f_nxt[o] + cc * fp[m]) * inv;
+            dc.f_cur[o] = fn[m];
+        }
+        T cv[D], c2 = 0;
+        for (int d = 0; d < D; ++d) {
+            cv[d] = u[d] - U[d];
+            c2 += cv[d] * cv[d];
+        }
+        const T we = dc.w[k] * (c2 * fn[0] + (NC == 2 ? fn[NC - 1] : T(0)));
+        for (int d = 0; d < D; ++d) acc[d] += cv[d] * we;
+    }
+    for (int d = 0; d < D; ++d) {
+        T s = warp_sum(acc[d]);
+        if (lane == 0) dc.q[(size_t)c * D + d] = 0.5 * (double)s;
+    }
+}
+
+// ------------------------------------------------------------ state I/O
+template <typename T, int D, int NC>
+__global__ void k_f_export(DevCase<T> dc, const long long *perm, int c0, int nc, double *out)
+{
+    // out[(i - c0)][m][k] (FP64, caller cell order i) from internal cell perm_inv...
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long per = (long long)NC * dc.nv;
+    if (idx >= (long long)nc * per) return;
+    const int i = c0 + (int)(idx / per);
+    const long long r = idx % per;
+    const int m = (int)(r / dc.nv), k = (int)(r % dc.nv);
+    const long long ci = perm[i];
+    out[idx] = (double)dc.f_cur[(size_t)ci * NC * dc.nvp + (size_t)m * dc.nvp + k];
+}
+
+template <typename T, int D, int NC>
+__global__ void k_f_import(DevCase<T> dc, const long long *perm, int c0, int nc, const double *in)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long per = (long long)NC * dc.nvp;
+    if (idx >= (long long)nc * per) return;
+    const int i = c0 + (int)(idx / per);
+    const long long r = idx % per;
+    const int m = (int)(r / dc.nvp), k = (int)(r % dc.nvp);
+    const long long ci = perm[i];
+    dc.f_cur[(size_t)ci * NC * dc.nvp + (size_t)m * dc.nvp + k] =
+        k < dc.nv ? (T)in[((long long)(i - c0) * NC + m) * dc.nv + k] : T(0);
+}
+
+template <int D>
+__global__ void k_moments_out(const double *W, const double *q, const long long *perm, int C, double *out)
+{
+    // out[i][0..]: rho, U[D], T, q[D] in caller order
+    constexpr int M = D + 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    const long long c = perm[i];
+    Prim p = prim_of(W + (size_t)c * M, D);
+    double *o = out + (size_t)i * (2 * D + 2);
+    o[0] = p.rho;
+    for (int d = 0; d < D; ++d) o[1 + d] = p.U[d];
+    o[D + 1] = p.T;
+    for (int d = 0; d < D; ++d) o[D + 2 + d] = q[(size_t)c * D + d];
+}
+
+template <int D>
+__global__ void k_W_permute(const double *src, const long long *perm, int C, double *dst, int to_internal)
+{
+    constexpr int M = D + 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    const long long c = perm[i];
+    for (int m = 0; m < M; ++m) {
+        if (to_internal) dst[(size_t)c * M + m] = src[(size_t)i * M + m];
+        else dst[(size_t)i * M + m] = src[(size_t)c * M + m];
+    }
+}
+
+__global__ void k_check(const double *W, int n, int M, int *flags)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const double *w = W + (size_t)c * M;
+    double ke = 0.0;
+    for (int d = 1; d < M - 1; ++d) ke += w[d] * w[d];
+    const double e = w[M - 1] - 0.5 * ke / w[0];
+    bool bad = !(w[0] > 0.0) || !(e > 0.0);
+    for (int m = 0; m < M; ++m) bad |= !isfinite(w[m]);
+    if (bad) atomicOr(flags, 1);
+}
+
+// ------------------------------------------------------------ launchers
+static inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
+
+template <typename T, int D, int NC, int TV>
+static cudaError_t gather_launch(const DevCase<T> &dc, size_t smem, cudaStream_t st)
+{
+    auto kern = k_gather<T, D, NC, TV>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(dc.n_patches, dc.n_vt);
+    kern<<<grid, 256, smem, st>>>(dc);
+    return cudaGetLastError();
+}
+
+template <typename T, int D, int NC>
+static cudaError_t step_dn(const DevCase<T> &dc, const StepConfig &cfg, cudaStream_t st, cudaEvent_t *ev)
+{
+    const int C = dc.C, F = dc.F;
+    // ev (optional): N_GROUPS + 1 events bracketing the kernel groups
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord(ev[i], st);
+    };
+    mark(0);
+    k_prep<T, D, NC><<<cdiv(C + dc.G, 128), 128, 0, st>>>(dc);
+    k_macro_grad<T, D, NC><<<cdiv(C, 128), 128, 0, st>>>(dc);
+    mark(1);
+    if (F > 0) {
+        k_face_pre<T, D, NC><<<cdiv(F, 128), 128, 0, st>>>(dc);
+        k_face_sum1<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
+        k_face_fin1<T, D, NC><<<cdiv(F, 128), 128, 0, st>>>(dc);
+        k_face_sum2<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
+        k_face_fin2<T, D, NC><<<cdiv(F, 64), 64, 0, st>>>(dc);
+    }
+    mark(2);
+    if (dc.NW > 0) k_wall_sum<T, D, NC><<<cdiv(dc.NW, 8), 256, 0, st>>>(dc);
+    mark(3);
+    cudaError_t e;
+    switch (dc.vtile / 32) {
+    case 1: e = gather_launch<T, D, NC, 1>(dc, cfg.smem, st); break;
+    case 2: e = gather_launch<T, D, NC, 2>(dc, cfg.smem, st); break;
+    case 4: e = gather_launch<T, D, NC, 4>(dc, cfg.smem, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    mark(4);
+    k_update_W<T, D, NC><<<cfg.n_res_blocks, 256, 0, st>>>(dc);
+    mark(5);
+    k_collide<T, D, NC><<<cdiv(C, 8), 256, 0, st>>>(dc);
+    mark(6);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_step(const DevCase<T> &dc, const StepConfig &cfg, cudaStream_t st, cudaEvent_t *ev)
+{
+    return dc.D == 2 ? step_dn<T, 2, 2>(dc, cfg, st, ev) : step_dn<T, 3, 1>(dc, cfg, st, ev);
+}
+
+template <typename T>
+cudaError_t launch_init(const DevCase<T> &dc, cudaStream_t st)
+{
+    if (dc.D == 2) {
+        k_init_f<T, 2, 2><<<cdiv(dc.C, 8), 256, 0, st>>>(dc);
+        k_heatflux<T, 2, 2><<<cdiv(dc.C, 8), 256, 0, st>>>(dc);
+    } else {
+        k_init_f<T, 3, 1><<<cdiv(dc.C, 8), 256, 0, st>>>(dc);
+        k_heatflux<T, 3, 1><<<cdiv(dc.C, 8), 256, 0, st>>>(dc);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_heatflux(const DevCase<T> &dc, cudaStream_t st)
+{
+    if (dc.D == 2) k_heatflux<T, 2, 2><<<cdiv(dc.C, 8), 256, 0, st>>>(dc);
+    else k_heatflux<T, 3, 1><<<cdiv(dc.C, 8), 256, 0, st>>>(dc);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_f_export(const DevCase<T> &dc, const long long *perm, int c0, int nc, double *out,
+                            cudaStream_t st)
+{
+    long long n = (long long)nc * (dc.D == 2 ? 2 : 1) * dc.nv;
+    if (n == 0) return cudaSuccess;
+    if (dc.D == 2) k_f_export<T, 2, 2><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, out);
+    else k_f_export<T, 3, 1><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_f_import(const DevCase<T> &dc, const long long *perm, int c0, int nc, const double *in,
+                            cudaStream_t st)
+{
+    long long n = (long long)nc * (dc.D == 2 ? 2 : 1) * dc.nvp;
+    if (n == 0) return cudaSuccess;
+    if (dc.D == 2) k_f_import<T, 2, 2><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, in);
+    else k_f_import<T, 3, 1><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const double *res_part, int nblocks, int D, double *res, cudaStream_t st)
+{
+    if (D == 2) k_residual<4><<<1, 32, 0, st>>>(res_part, nblocks, res);
+    else k_residual<5><<<1, 32, 0, st>>>(res_part, nblocks, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_out(const double *W, const double *q, const long long *perm, int C, int D,
+                               double *out, cudaStream_t st)
+{
+    if (C == 0) return cudaSuccess;
+    if (D == 2) k_moments_out<2><<<cdiv(C, 128), 128, 0, st>>>(W, q, perm, C, out);
+    else k_moments_out<3><<<cdiv(C, 128), 128, 0, st>>>(W, q, perm, C, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_W_permute(const double *src, const long long *perm, int C, int D, double *dst,
+                             int to_internal, cudaStream_t st)
+{
+    if (C == 0) return cudaSuccess;
+    if (D == 2) k_W_permute<2><<<cdiv(C, 128), 128, 0, st>>>(src, perm, C, dst, to_internal);
+    else k_W_permute<3><<<cdiv(C, 128), 128, 0, st>>>(src, perm, C, dst, to_internal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check(const double *W, int C, int M, int *flags, cudaStream_t st)
+{
+    if (C == 0) return cudaSuccess;
+    k_check<<<cdiv(C, 128), 128, 0, st>>>(W, C, M, flags);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step<double>(const DevCase<double> &, const StepConfig &, cudaStream_t, cudaEvent_t *);
+template cudaError_t launch_step<float>(const DevCase<float> &, const StepConfig &, cudaStream_t, cudaEvent_t *);
+template cudaError_t launch_init<double>(const DevCase<double> &, cudaStream_t);
+template cudaError_t launch_init<float>(const DevCase<float> &, cudaStream_t);
+template cudaError_t launch_heatflux<double>(const DevCase<double> &, cudaStream_t);
+template cudaError_t launch_heatflux<float>(const DevCase<float> &, cudaStream_t);
+template cudaError_t launch_f_export<double>(const DevCase<double> &, const long long *, int, int, double *, cudaStream_t);
+template cudaError_t launch_f_export<float>(const DevCase<float> &, const long long *, int, int, double *, cudaStream_t);
+template cudaError_t launch_f_import<double>(const DevCase<double> &, const long long *, int, int, const double *, cudaStream_t);
+template cudaError_t launch_f_import<float>(const DevCase<float> &, const long long *, int, int, const double *, cudaStream_t);
+
+}  // namespace ugks

@@ -1,0 +1,31 @@
+// ugks_kernels.h -- host-callable launchers of the UGKS kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ugks_device.cuh"
+
+namespace ugks {
+
+struct StepConfig {
+    size_t smem;        // dynamic shared memory of the gather kernel
+    int n_res_blocks;   // blocks of k_update_W (residual partials)
+};
+
+// kernel groups of one step, in launch order (timed by events when profiling)
+enum { G_PREP = 0, G_FACE = 1, G_WALL = 2, G_GATHER = 3, G_UPDATE = 4, G_COLLIDE = 5, N_GROUPS = 6 };
+template <typename T>
+cudaError_t launch_step(const DevCase<T> &dc, const StepConfig &cfg, cudaStream_t st, cudaEvent_t *ev = nullptr);
+template <typename T> cudaError_t launch_init(const DevCase<T> &dc, cudaStream_t st);
+template <typename T> cudaError_t launch_heatflux(const DevCase<T> &dc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_f_export(const DevCase<T> &dc, const long long *perm, int c0, int nc, double *out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_f_import(const DevCase<T> &dc, const long long *perm, int c0, int nc, const double *in, cudaStream_t st);
+cudaError_t launch_residual(const double *res_part, int nblocks, int D, double *res, cudaStream_t st);
+cudaError_t launch_moments_out(const double *W, const double *q, const long long *perm, int C, int D, double *out,
+                               cudaStream_t st);
+cudaError_t launch_W_permute(const double *src, const long long *perm, int C, int D, double *dst, int to_internal,
+                             cudaStream_t st);
+cudaError_t launch_check(const double *W, int C, int M, int *flags, cudaStream_t st);
+
+}  // namespace ugks

@@ -1,0 +1,85 @@
+"""The C ABI: the library loads, exports every entry point declared in
+include/ugks.h, and the ctypes structs match the C layout (no GPU needed)."""
+import ctypes as ct
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2412_06546_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ugks.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ugks_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "ugks_create" in names and "ugks_step" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(_lib.EXPORTS), set(names) - set(_lib.EXPORTS)
+
+
+def test_struct_layout_matches_header():
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "ugks.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(ugks_mesh), sizeof(ugks_vgrid), sizeof(ugks_params),
+         sizeof(ugks_alloc), sizeof(ugks_info_t));
+  printf("%zu %zu %zu %zu\n", offsetof(ugks_params, precision), offsetof(ugks_params, prim_init),
+         offsetof(ugks_params, vtile), offsetof(ugks_info_t, kernel_launches_per_step));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    sizes = [int(x) for x in out]
+    assert sizes[:5] == [ct.sizeof(_lib.Mesh), ct.sizeof(_lib.VGrid), ct.sizeof(_lib.Params),
+                         ct.sizeof(_lib.Alloc), ct.sizeof(_lib.Info)]
+    assert sizes[5:] == [_lib.Params.precision.offset, _lib.Params.prim_init.offset,
+                         _lib.Params.vtile.offset, _lib.Info.kernel_launches_per_step.offset]
+
+
+def test_errors_are_reported_without_a_gpu(lib):
+    """Invalid input is rejected with UGKS_EINVAL and a message before any
+    device call."""
+    from paper_2412_06546_gb300 import cases
+    case = cases.cavity_case(n=3, nv=4)
+    mesh = dict(case["mesh"])
+    mesh["cell_vol"] = mesh["cell_vol"].copy()
+    mesh["cell_vol"][1] = -1.0
+    (m, v, p), keep = _lib.make_structs(mesh, case["vgrid"], case["params"], case["init"])
+    h = ct.c_void_p()
+    code = lib.ugks_create(ct.byref(m), ct.byref(v), ct.byref(p), None, None, ct.byref(h))
+    assert code == 1 and b"volume" in lib.ugks_last_error()
+    assert not h.value
+
+
+def test_no_cpu_fallback_without_library(tmp_path):
+    with pytest.raises(RuntimeError, match="not built"):
+        saved = _lib._lib
+        try:
+            _lib._lib = None
+            _lib.load(str(tmp_path / "missing.so"))
+        finally:
+            _lib._lib = saved

@@ -1,0 +1,217 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Both sides start from the same seeded, perturbed (non-equilibrium) state and
+take the same steps; f, W and the heat flux are compared element by element.
+FP64 path: |delta| <= 1e-12 max|x| per element (and relative L2 <= 1e-12).
+FP32-storage path: relative L2 on W <= 1e-5 after 100 steps.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2412_06546_gb300 import _lib, cases as cs  # noqa: E402
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2412_06546_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _pair(case, precision=_lib.FP64, perturb=0.1, seed=1, params=None, init=None, **kw):
+    pr = params or case["params"]
+    ini = case["init"] if init is None else init
+    o = oracle.OracleCase(case["mesh"], case["vgrid"], pr, ini, n_threads=0)
+    g = _lib.Case(case["mesh"], case["vgrid"], pr, ini, precision=precision, **kw)
+    if perturb:
+        f0, W0, _ = o.state()
+        f0 = f0 * cs.perturbation(f0.shape, seed, perturb)
+        o.set_state(f0, W0)
+        g.set_state(f0, W0)
+    return o, g
+
+
+def _rel_max(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _compare(o, g, tol=TOL64, what=""):
+    fo, Wo, qo = o.state()
+    fg, Wg = g.state()
+    qg = g.heat_flux()
+    errs = {"f": _rel_max(fg, fo), "W": _rel_max(Wg, Wo),
+            "q": np.abs(qg - qo).max() / max(np.abs(qo).max(), 1e-3),
+            "f_l2": _rel_l2(fg, fo), "W_l2": _rel_l2(Wg, Wo)}
+    for k, v in errs.items():
+        assert v <= tol, (what, k, v, errs)
+    return errs
+
+
+def test_initial_state_matches():
+    case = cs.cavity_case()
+    o, g = _pair(case, perturb=0)
+    _compare(o, g, what="init")
+
+
+@pytest.mark.parametrize("steps", [1, 10])
+def test_cavity_fp64(steps):
+    case = cs.cavity_case()                        # 20x20 quads x 24^2, Shakhov
+    o, g = _pair(case)
+    o.step(steps)
+    g.step(steps)
+    _compare(o, g, what=f"cavity {steps}")
+    assert np.allclose(g.residual(), o.residual(), rtol=1e-9, atol=1e-15)
+
+
+def test_cylinder_walls_farfield_ragged_velocity_tail():
+    case = cs.cylinder_case(n_cells=2000, nvx=21, nvy=17, mach=5.0)   # Nv = 357 (ragged)
+    o, g = _pair(case, perturb=0.05)
+    o.step(2)
+    g.step(2)
+    _compare(o, g, what="cylinder")
+
+
+def test_periodic_shakhov_smooth_state():
+    mesh = cs.periodic_tri_mesh(9, 7, 1.0, 0.8, jitter=0.25, seed=4)
+    case = {"mesh": mesh, "vgrid": cs.cartesian_vgrid((12, 10), (-5, -4.5), (5, 4.5)),
+            "params": cs.params(0.03), "init": cs.smooth_state(mesh, 5, 0.15, U0=[0.3, -0.2])}
+    o, g = _pair(case, perturb=0.2)
+    o.step(3)
+    g.step(3)
+    _compare(o, g, what="periodic")
+
+
+def test_3d_box_moving_wall():
+    mesh = cs.hex_mesh(4, 4, 3, sides={"x-": ("wall", 0), "x+": ("wall", 0), "y-": ("wall", 0),
+                                       "y+": ("wall", 0), "z-": ("wall", 0), "z+": ("wall", 1)})
+    vg = cs.cartesian_vgrid((9, 8, 7), (-4, -4, -4), (4, 4, 4))
+    pr = cs.params(0.1, walls=[{"T": 1.0, "U": [0, 0, 0]}, {"T": 1.2, "U": [0.3, 0.1, 0]}])
+    case = {"mesh": mesh, "vgrid": vg, "params": pr, "init": cs.smooth_state(mesh, 2, 0.1)}
+    o, g = _pair(case, perturb=0.1)
+    o.step(2)
+    g.step(2)
+    _compare(o, g, what="3d box")
+
+
+def test_3d_sphere_tetrahedra():
+    case = cs.sphere_case(n_cells=3000, nv=8, vmax=8.0, mach=2.0)
+    o, g = _pair(case, perturb=0.05)
+    o.step(1)
+    g.step(1)
+    _compare(o, g, what="sphere")
+
+
+@pytest.mark.parametrize("variant", ["free_molecular", "no_limiter", "bgk"])
+def test_limits_and_options(variant):
+    case = cs.cylinder_case(n_cells=1200, nvx=16, nvy=14, mach=3.0)
+    pr = dict(case["params"])
+    if variant == "free_molecular":
+        pr["Kn"] = float("inf")
+    elif variant == "no_limiter":
+        pr["limiter"] = 0
+    else:
+        pr["Pr"] = 1.0
+    o, g = _pair(case, params=pr, perturb=0.05)
+    o.step(2)
+    g.step(2)
+    _compare(o, g, what=variant)
+
+
+@pytest.mark.parametrize("patch,vtile", [(4, 32), (17, 64), (64, 128), (200, 32)])
+def test_tiling_does_not_change_results(patch, vtile):
+    case = cs.cylinder_case(n_cells=1500, nvx=18, nvy=15, mach=4.0)
+    o, g = _pair(case, perturb=0.05, patch_cells=patch, vtile=vtile)
+    info = g.info()
+    assert info["patch_cells"] <= patch and info["vtile"] == vtile
+    o.step(1)
+    g.step(1)
+    _compare(o, g, what=f"tiling {patch}/{vtile}")
+
+
+def test_runs_are_bitwise_deterministic():
+    case = cs.cylinder_case(n_cells=1500, nvx=16, nvy=14)
+    outs = []
+    for _ in range(2):
+        g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32)
+        g.step(5)
+        outs.append(g.state())
+        g.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_fp32_storage_form_cavity_100_steps():
+    case = cs.cavity_case()
+    o = oracle.OracleCase(case["mesh"], case["vgrid"], case["params"], case["init"])
+    g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32)
+    o.step(100)
+    g.step(100)
+    fo, Wo, qo = o.state()
+    fg, Wg = g.state()
+    eW = _rel_l2(Wg, Wo)
+    ef = _rel_l2(fg, fo)
+    # the velocity field is what changes: its error relative to its own size
+    U_o = Wo[:, 1:3] / Wo[:, :1]
+    U_g = Wg[:, 1:3] / Wg[:, :1]
+    eU = _rel_l2(U_g, U_o)
+    print(f"fp32 cavity 100 steps: W {eW:.2e} f {ef:.2e} U {eU:.2e}")
+    assert eW <= 1e-5 and ef <= 1e-5 and eU <= 1e-4
+
+
+def test_fp32_storage_form_cylinder_100_steps():
+    case = cs.cylinder_case(n_cells=2000, nvx=30, nvy=25)
+    o = oracle.OracleCase(case["mesh"], case["vgrid"], case["params"], case["init"])
+    g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32)
+    o.step(100)
+    g.step(100)
+    _, Wo, _ = o.state()
+    _, Wg = g.state()
+    eW = _rel_l2(Wg, Wo)
+    print(f"fp32 cylinder 100 steps: W {eW:.2e}")
+    assert eW <= 1e-5
+
+
+def test_numeric_failure_is_reported():
+    case = cs.cavity_case(n=4, nv=8)
+    g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"])
+    _, W = g.state(with_f=False)
+    W[2, 3] = -1.0                                    # negative energy
+    g.set_state(None, W)
+    with pytest.raises(_lib.UGKSError) as e:
+        g.check()
+    assert e.value.code == 4
+
+
+def test_full_size_cylinder_one_step_fp64():
+    """The 30k-cell x 60x50 cylinder at full size, FP64, one step from a
+    perturbed state: every element against the oracle."""
+    case = cs.cylinder_case()
+    o, g = _pair(case, perturb=0.05)
+    o.step(1)
+    g.step(1)
+    _compare(o, g, what="cylinder full size")
+
+
+def test_impulsive_mach5_start_full_size_fp32_stays_physical():
+    """The 30k-cell Mach-5 cylinder, FP32 form, 300 steps from the impulsive
+    start: the state stays finite with positive density and temperature."""
+    case = cs.cylinder_case()
+    g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32)
+    for _ in range(3):
+        g.step(100)
+        g.check()
+    rho, U, T, q = g.moments()
+    assert rho.min() > 0 and T.min() > 0 and np.isfinite(q).all()
