@@ -56,7 +56,7 @@ struct or_case {
     double *f, *W;
     /* per-step work arrays */
     double *Wold, *q, *rho, *U, *lam, *tau, *gradW, *Wghost, *W0, *fa, *fA, *q0, *qs, *grad_k,
-        *Fk, *Fm, *fin, *gfin, *rho_w, *ghost_k, res[MAXM];
+        *Fk, *Fm, *fin, *gfin, *rho_w, *ghost_k, res[MAXM], *P, *Pg, *gradP;
 };
 
 /* ------------------------------------------------------------------------ */
@@ -550,6 +550,9 @@ or_case *or_create(const or_mesh *m, const or_vgrid *v, const or_params *p,
     c->lam = (double *)malloc(sizeof(double) * C);
     c->tau = (double *)malloc(sizeof(double) * C);
     c->gradW = (double *)malloc(sizeof(double) * C * D * M);
+    c->gradP = (double *)malloc(sizeof(double) * C * D * M);
+    c->P = (double *)malloc(sizeof(double) * C * M);
+    c->Pg = (double *)malloc(sizeof(double) * (F ? F : 1) * M);
     c->Wghost = (double *)malloc(sizeof(double) * (F ? F : 1) * M);
     c->W0 = (double *)malloc(sizeof(double) * (F ? F : 1) * M);
     c->fa = (double *)malloc(sizeof(double) * (F ? F : 1) * D * M);
@@ -605,7 +608,7 @@ void or_destroy(or_case *c)
                     c->eps2, c->wall_face, c->wall_slot_of_face, c->f, c->W, c->Wold, c->q,
                     c->rho, c->U, c->lam, c->tau, c->gradW, c->Wghost, c->W0, c->fa, c->fA,
                     c->q0, c->qs, c->grad_k, c->Fk, c->Fm, c->fin, c->gfin, c->rho_w,
-                    c->ghost_k};
+                    c->ghost_k, c->P, c->Pg, c->gradP};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(c);
 }
@@ -703,21 +706,37 @@ void or_scalar_gradient(or_case *c, const double *phi, const double *phi_ghost, 
     free(gv);
 }
 
-/* face state W_i + grad W_i . r with a positivity fallback
- * (READING: if rho or the thermal energy of the extrapolated state is not
- * positive, the cell average is used on that side). */
+/* face state from the primitive reconstruction P_i + grad P_i . r, returned
+ * as conserved variables, with a positivity fallback (READING: if rho or T of
+ * the extrapolated state is not positive, the cell average is used). */
 static void face_state(const or_case *c, int64_t i, const double *r, double *Ws)
 {
     int D = c->D, M = D + 2;
+    double pf[MAXM];
     for (int m = 0; m < M; ++m) {
-        double s = c->W[i * M + m];
-        for (int d = 0; d < D; ++d) s += c->gradW[(i * D + d) * M + m] * r[d];
-        Ws[m] = s;
+        double s = c->P[i * M + m];
+        for (int d = 0; d < D; ++d) s += c->gradP[(i * D + d) * M + m] * r[d];
+        pf[m] = s;
     }
+    if (!(pf[0] > 0.0) || !(pf[D + 1] > 0.0))
+        for (int m = 0; m < M; ++m) pf[m] = c->P[i * M + m];
     double ke = 0.0;
-    for (int d = 0; d < D; ++d) ke += Ws[1 + d] * Ws[1 + d];
-    if (!(Ws[0] > 0.0) || !(Ws[D + 1] - 0.5 * ke / Ws[0] > 0.0))
-        for (int m = 0; m < M; ++m) Ws[m] = c->W[i * M + m];
+    Ws[0] = pf[0];
+    for (int d = 0; d < D; ++d) {
+        Ws[1 + d] = pf[0] * pf[1 + d];
+        ke += pf[1 + d] * pf[1 + d];
+    }
+    Ws[D + 1] = pf[0] * (0.5 * ke + 1.5 * pf[D + 1]);
+}
+
+/* primitive variables (rho, U, T) of a conserved state */
+static void to_primitive(int D, const double *W, double *P)
+{
+    double rho, U[MAXD], lam;
+    prim_of(D, W, &rho, U, &lam);
+    P[0] = rho;
+    for (int d = 0; d < D; ++d) P[1 + d] = U[d];
+    P[D + 1] = 1.0 / (2.0 * lam);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -776,15 +795,39 @@ static void one_step(or_case *c)
     }
 
     /* ---- Alg. 1 line 2: macroscopic reconstruction ----
-     * READING: the "gradient compressor factors" of the cited sliding-mesh
-     * paper are taken as Venkatakrishnan factors on each conserved component
-     * of the least-squares gradient (the same limiter as the micro slopes). */
+     * READING: the "gradients of macroscopic values" are least-squares
+     * gradients of the primitive variables (rho, U, T), and the "gradient
+     * compressor factors" of the cited sliding-mesh paper are taken as
+     * Venkatakrishnan factors on each of them (the limiter of the micro
+     * slopes).  Face states are reconstructed from these, so the face
+     * temperature stays within the range of the neighbours'; limiting the
+     * conserved components separately can leave a face temperature far below
+     * every neighbour's, whose Maxwellian the velocity grid cannot resolve.
+     * The conserved-variable gradient used for the slopes of g0 is the chain
+     * rule of the limited primitive gradient at the cell state. */
+    for (int64_t i = 0; i < C; ++i) to_primitive(D, c->W + i * M, c->P + i * M);
+    for (int64_t f = 0; f < F; ++f)
+        if (c->face_type[f] == OR_FARFIELD) to_primitive(D, c->Wghost + f * M, c->Pg + f * M);
 #pragma omp parallel for num_threads(nt) schedule(static)
     for (int64_t i = 0; i < C; ++i) {
+        const double *Pi = c->P + i * M;
         for (int m = 0; m < M; ++m) {
             double g[MAXD];
-            lsq_gradient(c, i, c->W + m, M, c->Wghost + m, M, c->p.limiter, g);
-            for (int d = 0; d < D; ++d) c->gradW[(i * D + d) * M + m] = g[d];
+            lsq_gradient(c, i, c->P + m, M, c->Pg + m, M, c->p.limiter, g);
+            for (int d = 0; d < D; ++d) c->gradP[(i * D + d) * M + m] = g[d];
+        }
+        double uu = 0.0;
+        for (int e = 0; e < D; ++e) uu += Pi[1 + e] * Pi[1 + e];
+        for (int d = 0; d < D; ++d) {
+            const double *gp = c->gradP + (i * D + d) * M;
+            double *gw = c->gradW + (i * D + d) * M;
+            double udu = 0.0;
+            gw[0] = gp[0];
+            for (int e = 0; e < D; ++e) {
+                gw[1 + e] = Pi[1 + e] * gp[0] + Pi[0] * gp[1 + e];
+                udu += Pi[1 + e] * gp[1 + e];
+            }
+            gw[D + 1] = gp[0] * (0.5 * uu + 1.5 * Pi[D + 1]) + Pi[0] * (udu + 1.5 * gp[D + 1]);
         }
     }
 
