@@ -46,6 +46,7 @@ struct DevCase {
     T *f_cur, *f_nxt;
     // macroscopic state
     double *W, *q, *gradW, *vol;
+    double *prim, *primg, *gradprim;  // primitive (rho, U, T) of cells / ghosts, limited gradient
     // least squares (CSR over cells)
     const int *nb_ptr, *nb_id;    // id >= 0: cell, id < 0: ghost -(id+1)
     const double *nb_a_d;

@@ -491,6 +491,9 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     dc.W = c->upload(W);
     dc.q = (double *)c->dalloc((size_t)c->C * D * sizeof(double));
     dc.gradW = (double *)c->dalloc((size_t)c->C * D * M * sizeof(double));
+    dc.gradprim = (double *)c->dalloc((size_t)c->C * D * M * sizeof(double));
+    dc.prim = (double *)c->dalloc((size_t)c->C * M * sizeof(double));
+    dc.primg = (double *)c->dalloc((size_t)std::max(c->G, 1) * M * sizeof(double));
     dc.vol = c->upload(h.vol);
     dc.nb_ptr = c->upload(h.nb_ptr);
     dc.nb_id = c->upload(h.nb_id);

@@ -171,6 +171,10 @@ __global__ void k_prep(DevCase<T> dc)
         const int c = t;
         Prim p = prim_of(dc.W + (size_t)c * M, D);
         if (!(p.rho > 0.0) || !(p.T > 0.0)) atomicOr(dc.flags, 1);
+        double *Pc = dc.prim + (size_t)c * M;
+        Pc[0] = p.rho;
+        for (int d = 0; d < D; ++d) Pc[1 + d] = p.U[d];
+        Pc[D + 1] = p.T;
         double tau = tau_of(dc, p.rho, p.T);
         double kappa = 4.0 * (1.0 - dc.Pr) * p.lam * p.lam / (5.0 * p.rho);
         T *r = dc.crec + (size_t)c * CREC;
@@ -194,6 +198,10 @@ __global__ void k_prep(DevCase<T> dc)
     double *Wg = dc.Wg + (size_t)g * M;
     for (int m = 0; m < M; ++m) Wg[m] = un < 0.0 ? dc.inf_W[m] : dc.W[(size_t)own * M + m];
     Prim p = prim_of(Wg, D);
+    double *Pg = dc.primg + (size_t)g * M;
+    Pg[0] = p.rho;
+    for (int d = 0; d < D; ++d) Pg[1 + d] = p.U[d];
+    Pg[D + 1] = p.T;
     T *r = dc.grec + (size_t)g * GREC;
     for (int d = 0; d < 3; ++d) r[GR_U + d] = (T)p.U[d];
     r[GR_LAM] = (T)p.lam;
@@ -202,23 +210,26 @@ __global__ void k_prep(DevCase<T> dc)
 }
 
 // ------------------------------------------------------------ k_macro_grad
+// limited least-squares gradients of the primitive variables (rho, U, T) and
+// the conserved-variable gradient obtained from them by the chain rule
 template <typename T, int D, int NC>
 __global__ void k_macro_grad(DevCase<T> dc)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     constexpr int M = D + 2;
     if (c >= dc.C) return;
-    const double *Wc = dc.W + (size_t)c * M;
+    const double *Pc = dc.prim + (size_t)c * M;
     const int q0 = dc.nb_ptr[c], q1 = dc.nb_ptr[c + 1];
     const int s0 = dc.cf_ptr[c], s1 = dc.cf_ptr[c + 1];
     const double e2 = dc.eps2_d[c];
+    double gp[D][M];
     for (int m = 0; m < M; ++m) {
-        const double vi = Wc[m];
+        const double vi = Pc[m];
         double g[D], vmax = vi, vmin = vi;
         for (int d = 0; d < D; ++d) g[d] = 0.0;
         for (int q = q0; q < q1; ++q) {
             const int id = dc.nb_id[q];
-            const double vj = id >= 0 ? dc.W[(size_t)id * M + m] : dc.Wg[(size_t)(-id - 1) * M + m];
+            const double vj = id >= 0 ? dc.prim[(size_t)id * M + m] : dc.primg[(size_t)(-id - 1) * M + m];
             for (int d = 0; d < D; ++d) g[d] += dc.nb_a_d[(size_t)q * D + d] * (vj - vi);
             vmax = fmax(vmax, vj);
             vmin = fmin(vmin, vj);
@@ -233,27 +244,49 @@ __global__ void k_macro_grad(DevCase<T> dc)
             }
             for (int d = 0; d < D; ++d) g[d] *= phi;
         }
-        for (int d = 0; d < D; ++d) dc.gradW[((size_t)c * D + d) * M + m] = g[d];
+        for (int d = 0; d < D; ++d) {
+            gp[d][m] = g[d];
+            dc.gradprim[((size_t)c * D + d) * M + m] = g[d];
+        }
+    }
+    double uu = 0.0;
+    for (int e = 0; e < D; ++e) uu += Pc[1 + e] * Pc[1 + e];
+    for (int d = 0; d < D; ++d) {
+        double *gw = dc.gradW + ((size_t)c * D + d) * M;
+        double udu = 0.0;
+        gw[0] = gp[d][0];
+        for (int e = 0; e < D; ++e) {
+            gw[1 + e] = Pc[1 + e] * gp[d][0] + Pc[0] * gp[d][1 + e];
+            udu += Pc[1 + e] * gp[d][1 + e];
+        }
+        gw[D + 1] = gp[d][0] * (0.5 * uu + 1.5 * Pc[D + 1]) + Pc[0] * (udu + 1.5 * gp[d][D + 1]);
     }
 }
 
 // ------------------------------------------------------------ face pass
-// face state W_c + gradW_c . r, falling back to W_c if rho or the thermal
-// energy would not be positive
+// face state reconstructed in primitive variables, P_c + gradP_c . r, returned
+// as conserved variables; the cell average is used if rho or T would not be
+// positive
 template <int D>
-__device__ __forceinline__ void face_state(const double *W, const double *gradW, int c, const double *r,
+__device__ __forceinline__ void face_state(const double *P, const double *gradP, int c, const double *r,
                                            double *Ws)
 {
     constexpr int M = D + 2;
+    double pf[M];
     for (int m = 0; m < M; ++m) {
-        double s = W[(size_t)c * M + m];
-        for (int d = 0; d < D; ++d) s += gradW[((size_t)c * D + d) * M + m] * r[d];
-        Ws[m] = s;
+        double s = P[(size_t)c * M + m];
+        for (int d = 0; d < D; ++d) s += gradP[((size_t)c * D + d) * M + m] * r[d];
+        pf[m] = s;
     }
+    if (!(pf[0] > 0.0) || !(pf[D + 1] > 0.0))
+        for (int m = 0; m < M; ++m) pf[m] = P[(size_t)c * M + m];
     double ke = 0.0;
-    for (int d = 0; d < D; ++d) ke += Ws[1 + d] * Ws[1 + d];
-    if (!(Ws[0] > 0.0) || !(Ws[D + 1] - 0.5 * ke / Ws[0] > 0.0))
-        for (int m = 0; m < M; ++m) Ws[m] = W[(size_t)c * M + m];
+    Ws[0] = pf[0];
+    for (int d = 0; d < D; ++d) {
+        Ws[1 + d] = pf[0] * pf[1 + d];
+        ke += pf[1 + d] * pf[1 + d];
+    }
+    Ws[D + 1] = pf[0] * (0.5 * ke + 1.5 * pf[D + 1]);
 }
 
 template <typename T, int D>
@@ -277,7 +310,7 @@ __global__ void k_face_pre(DevCase<T> dc)
     const int L = dc.fL[f];
     double WL[M], WR[M], rL[D], rR[D];
     for (int d = 0; d < D; ++d) rL[d] = dc.frL_d[(size_t)f * D + d];
-    face_state<D>(dc.W, dc.gradW, L, rL, WL);
+    face_state<D>(dc.prim, dc.gradprim, L, rL, WL);
     double *dW0 = dc.fdW0 + (size_t)f * D * M;
     double *q0 = dc.fq0 + (size_t)f * D;
     if (typ == FT_FARFIELD) {
@@ -290,7 +323,7 @@ __global__ void k_face_pre(DevCase<T> dc)
     } else {
         const int R = dc.fR[f];
         for (int d = 0; d < D; ++d) rR[d] = dc.frR_d[(size_t)f * D + d];
-        face_state<D>(dc.W, dc.gradW, R, rR, WR);
+        face_state<D>(dc.prim, dc.gradprim, R, rR, WR);
         for (int d = 0; d < D; ++d) {
             for (int m = 0; m < M; ++m)
                 dW0[d * M + m] = 0.5 * (dc.gradW[((size_t)L * D + d) * M + m] + dc.gradW[((size_t)R * D + d) * M + m]);
