@@ -473,21 +473,40 @@ def freestream_speed(mach, gamma=5.0 / 3.0, T=1.0):
     return mach * math.sqrt(gamma * T)
 
 
+def blended_start(mesh, U, r_body=1.0, delta=1.0):
+    """Initial field for flow past a body of radius ``r_body`` centred at the
+    origin: rho = T = 1 and a velocity that rises from rest at the wall to the
+    free stream, U(r) = U_inf (1 - exp(-(r - r_body)/delta)).  It avoids the
+    transient near-vacuum that an impulsive uniform start opens behind the
+    body; the steady state does not depend on it."""
+    D = mesh["dim"]
+    r = np.linalg.norm(mesh["cell_xc"], axis=1)
+    s = 1.0 - np.exp(-np.maximum(r - r_body, 0.0) / delta)
+    init = uniform_state(len(r), D)
+    init[:, 1:1 + D] = s[:, None] * np.asarray(U, float)[None, :D]
+    return init
+
+
 def cylinder_case(n_cells=30000, nvx=60, nvy=50, mach=5.0, Kn=0.1, seed=2,
-                  vx=(-12.0, 12.0), vy=(-10.0, 10.0)):
+                  vx=(-12.0, 12.0), vy=(-10.0, 10.0), start="blended"):
     """2D Mach-``mach`` argon flow past a radius-1 cylinder, far field at radius
-    15; Kn defined on the diameter (L_ref = 2); isothermal wall at T_inf = 1."""
+    15; Kn defined on the diameter (L_ref = 2); isothermal wall at T_inf = 1.
+    ``start``: "blended" (rest at the wall, free stream away from it) or
+    "impulsive" (uniform free stream)."""
     mesh = cylinder_mesh(n_cells, seed=seed)
     vg = cartesian_vgrid((nvx, nvy), (vx[0], vy[0]), (vx[1], vy[1]))
     Uinf = freestream_speed(mach)
     pr = params(Kn, L_ref=2.0, walls=[{"T": 1.0, "U": [0.0, 0.0, 0.0]}],
                 inf={"rho": 1.0, "U": [Uinf, 0.0, 0.0], "T": 1.0})
-    init = uniform_state(len(mesh["cell_vol"]), 2, U=[Uinf, 0.0])
+    if start == "impulsive":
+        init = uniform_state(len(mesh["cell_vol"]), 2, U=[Uinf, 0.0])
+    else:
+        init = blended_start(mesh, [Uinf, 0.0])
     return {"name": f"cylinder_Ma{mach:g}_Kn{Kn:g}_c{len(mesh['cell_vol'])}_v{nvx}x{nvy}",
             "mesh": mesh, "vgrid": vg, "params": pr, "init": init}
 
 
-def sphere_case(n_cells=150000, nv=28, vmax=10.0, mach=4.0, Kn=0.1, seed=3):
+def sphere_case(n_cells=150000, nv=28, vmax=10.0, mach=4.0, Kn=0.1, seed=3, start="blended"):
     """3D Mach-``mach`` argon flow past a radius-1 sphere, far field at radius
     12, Kn on the diameter; nv^3 velocities on [-vmax, vmax]^3."""
     mesh = sphere_mesh(n_cells, seed=seed)
@@ -495,7 +514,10 @@ def sphere_case(n_cells=150000, nv=28, vmax=10.0, mach=4.0, Kn=0.1, seed=3):
     Uinf = freestream_speed(mach)
     pr = params(Kn, Pr=2.0 / 3.0, L_ref=2.0, walls=[{"T": 1.0, "U": [0.0, 0.0, 0.0]}],
                 inf={"rho": 1.0, "U": [Uinf, 0.0, 0.0], "T": 1.0})
-    init = uniform_state(len(mesh["cell_vol"]), 3, U=[Uinf, 0.0, 0.0])
+    if start == "impulsive":
+        init = uniform_state(len(mesh["cell_vol"]), 3, U=[Uinf, 0.0, 0.0])
+    else:
+        init = blended_start(mesh, [Uinf, 0.0, 0.0])
     return {"name": f"sphere_Ma{mach:g}_Kn{Kn:g}_c{len(mesh['cell_vol'])}_v{nv}^3",
             "mesh": mesh, "vgrid": vg, "params": pr, "init": init}
 

@@ -591,7 +591,7 @@ def test_impulsive_hypersonic_start_stays_physical():
     """Mach 5 impulsively started cylinder (Shakhov): the near wake empties
     towards vacuum and the wall Knudsen layer carries |q| ~ p sqrt(T) within a
     few steps; density and temperature stay positive throughout."""
-    case = cs.cylinder_case(n_cells=2000, nvx=30, nvy=25, mach=5.0)
+    case = cs.cylinder_case(n_cells=2000, nvx=30, nvy=25, mach=5.0, start="impulsive")
     o = oracle.OracleCase(case["mesh"], case["vgrid"], case["params"], case["init"])
     for _ in range(20):
         o.step(5)
