@@ -173,6 +173,30 @@ ugks_status ugks_info(const ugks_case *c, ugks_info_t *info);
 /* Release the device memory of a case (NULL is ignored). */
 void ugks_destroy(ugks_case *c);
 
+/* Residual of two conserved-variable states held on the device, computed
+ * without allocating any device memory.  For callers that cannot call
+ * cudaMalloc: code running under an external memory manager that has already
+ * reserved the device memory, a serving loop that admits work against a fixed
+ * device budget, or a monitoring hook that must not synchronise the device.
+ * The paper has no counterpart; it returns the same quantity as ugks_residual.
+ *   W_old, W_new: device pointers, [n_cells][dim+2] conserved variables, the
+ *                 same cell order in both; read only.
+ *   res:          device pointer to dim+2 doubles (caller-owned), receives
+ *                 |W_new_m - W_old_m|_2 / |W_old_m|_2 per component.
+ *   stream:       cudaStream_t the two kernels are issued on (NULL: legacy
+ *                 default stream); the call is asynchronous.
+ * Limit: n_cells <= 2,097,152 (UGKS_EINVAL above it).  The block partial sums
+ * live in a fixed 655 KB file-scope device array that every device which loads
+ * the library holds until the process exits.  The first call on a device looks
+ * up that array's device address (once, with that device current), so make
+ * the first call on each device before any stream capture.  All calls share
+ * the array: calls whose kernels overlap on the GPU race and give wrong
+ * results.  Each call writes every partial it reads, so nothing carries over
+ * from an earlier call.  No cudaMalloc, cudaFree or allocating routine is
+ * called. */
+ugks_status ugks_residual_noalloc(const double *W_old, const double *W_new, int64_t n_cells, int32_t dim,
+                                  double *res, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *ugks_last_error(void);
 

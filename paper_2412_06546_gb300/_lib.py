@@ -81,6 +81,8 @@ EXPORTS = {
     "ugks_info": (ct.c_int, [ct.c_void_p, ct.POINTER(Info)]),
     "ugks_profile_begin": (ct.c_int, [ct.c_void_p, ct.c_int32]),
     "ugks_profile_end": (ct.c_int, [ct.c_void_p, D_P, ct.c_int32, ct.POINTER(ct.c_int32)]),
+    "ugks_residual_noalloc": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p,
+                                         ct.c_void_p]),
     "ugks_destroy": (None, [ct.c_void_p]),
     "ugks_last_error": (ct.c_char_p, []),
 }

@@ -595,6 +595,11 @@ auto with_dc(ugks_case *c, Fn &&fn)
 }
 }  // namespace
 
+namespace ugks {
+// lets other translation units of the library report through ugks_last_error()
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace ugks
+
 extern "C" {
 
 const char *ugks_last_error(void) { return g_err.c_str(); }
