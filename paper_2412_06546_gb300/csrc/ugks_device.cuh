@@ -20,13 +20,23 @@ constexpr int MAXD = 3;
 constexpr int MAXM = 5;
 
 // cell record: Maxwellian of the cell state plus Shakhov and collision factors
-enum { CR_U = 0, CR_LAM = 3, CR_PREF = 4, CR_KQ = 5, CR_C = 8, CR_NB = 9, CREC = 12 };
+enum { CR_U = 0, CR_LAM = 3, CR_PREF = 4, CR_KQ = 5, CR_C = 8, CR_NB = 9, CR_NL2 = 10, CREC = 12 };
 // ghost / side / wall record: a Maxwellian
-enum { GR_U = 0, GR_LAM = 3, GR_PREF = 4, GR_NB = 5, GREC = 8 };
+enum { GR_U = 0, GR_LAM = 3, GR_PREF = 4, GR_NB = 5, GR_NL2 = 6, GREC = 8 };
 // face record: g0 of the interface, Shakhov factor, time integrals, slopes in
 // the basis centred at U0: psi_c = (1, c, (|c|^2 + xi^2)/2), c = u - U0
 enum { FR_U = 0, FR_LAM = 3, FR_PREF = 4, FR_KQ = 5, FR_QS = 8, FR_NB = 13, FR_XB = 14,
-       FR_BETA = 15, FREC = 40 };
+       FR_BETA = 15, FR_NL2 = 39, FREC = 40 };
+
+// flux record read by the gather pass: the equilibrium part of the
+// time-integrated interface distribution, q3 (g0 + g0+) + q4 u.grad g0 +
+// q5 dg0/dt, is H0(c) P_m(c) with c = u - U0 and, per stored component m,
+// P_m(c) = a0 + a.c + sum_{e<=f} B_ef c_e c_f + (gamma.c)|c|^2
+enum { XR_U = 0, XR_PREF = 3, XR_NL2 = 4, XR_LAM = 5, XR_Q1 = 6, XR_Q2 = 7, XR_POLY = 8, XREC = 24 };
+template <int D> struct Poly {
+    static constexpr int NB = D * (D + 1) / 2;
+    static constexpr int N = 1 + D + NB + D;   // a0, a, B (packed upper, off-diagonal doubled), gamma
+};
 
 enum { FT_INTERIOR = 0, FT_WALL = 1, FT_FARFIELD = 2, FT_PERIODIC = 3 };
 
@@ -64,7 +74,8 @@ struct DevCase {
     const int *fL, *fR, *faux;    // owner, neighbour (-1 at boundaries), ghost or wall slot
     const signed char *ftype;
     const double *fn_d, *frL_d, *frR_d;
-    const T *fn;
+    const T *fn, *frL, *frR;      // T copies used inside velocity loops
+    T dtT;                        // dt in the arithmetic type
     // ghosts (one per far-field face)
     const int *gface;
     double *Wg;                   // [G][D+2]
@@ -79,7 +90,8 @@ struct DevCase {
     // per-step work
     T *crec;                      // [C][CREC] stage-1 record (W^n, q^n)
     T *krec;                      // [C][CREC] stage-2 record (W^{n+1}, q^n)
-    T *frec;                      // [F][FREC]
+    T *frec;                      // [F][FREC] face-pass work record
+    T *xrec;                      // [F][XREC] flux record of the gather pass
     T *fside;                     // [F][2][GREC] Maxwellians of the face states
     double *fdW0;                 // [F][D][D+2] interface macro gradient
     double *fq0;                  // [F][D]
@@ -98,6 +110,25 @@ struct DevCase {
 template <typename T> __device__ __forceinline__ T dexp(T x);
 template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
 template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
+
+// 2^x with the hardware approximation (relative error ~2^-22); FP32 only
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// exp(-lambda c2) of a record: FP64 through exp(), FP32 through 2^(nl2 c2)
+// with nl2 = -lambda log2(e) precomputed in the record
+template <typename T> __device__ __forceinline__ T gauss(T lam, T nl2, T c2);
+template <> __device__ __forceinline__ double gauss<double>(double lam, double, double c2) { return exp(-lam * c2); }
+template <> __device__ __forceinline__ float gauss<float>(float, float nl2, float c2) { return ex2_approx(nl2 * c2); }
+
+// a / b: IEEE in FP64, the fast reciprocal-based quotient in FP32
+template <typename T> __device__ __forceinline__ T fdiv(T a, T b);
+template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
 
 template <typename T> __device__ __forceinline__ T mul_rn(T a, T b);
 template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
@@ -125,6 +156,34 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Sum of N (4 or 8) values over the 32 lanes of a warp by recursive halving:
+// at every exchange a lane keeps half of its values and receives the
+// partner's partial sums of that half.  On return lane l holds the full sum
+// of value index l >> (5 - log2 N) (lanes 8j..8j+7 for N = 4).
+template <typename T, int N>
+__device__ __forceinline__ T warp_transpose_sum(T (&v)[N])
+{
+    const int lane = threadIdx.x & 31;
+    int n = N;
+#pragma unroll
+    for (int bit = 16; n > 1; bit >>= 1) {
+        n >>= 1;
+        const bool upper = (lane & bit) != 0;
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            if (i >= n) break;
+            const T send = upper ? v[i] : v[i + n];
+            const T keep = upper ? v[i + n] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+        }
+    }
+    constexpr int used = (N == 8) ? 3 : (N == 4 ? 2 : (N == 2 ? 1 : 0));
+    T r = v[0];
+#pragma unroll
+    for (int bit = 16 >> used; bit > 0; bit >>= 1) r += __shfl_xor_sync(0xffffffffu, r, bit);
+    return r;
+}
+
 // Maxwellian H and the b-factor of a record (cell / ghost / side / wall)
 template <typename T, int D>
 __device__ __forceinline__ T maxwell_h(const T *rec, const T u[3])
@@ -135,7 +194,7 @@ __device__ __forceinline__ T maxwell_h(const T *rec, const T u[3])
         T c = u[d] - rec[GR_U + d];
         c2 += c * c;
     }
-    return rec[GR_PREF] * dexp(-rec[GR_LAM] * c2);
+    return rec[GR_PREF] * gauss<T>(rec[GR_LAM], rec[GR_NL2], c2);
 }
 
 // Shakhov equilibrium f+ = (H + H+, B + B+) of a cell record at velocity u:
@@ -150,7 +209,7 @@ __device__ __forceinline__ void shakhov_fplus(const T *rec, const T u[3], T fp[N
         c2 += c[d] * c[d];
         kqc += rec[CR_KQ + d] * c[d];
     }
-    T H = rec[CR_PREF] * dexp(-rec[CR_LAM] * c2);
+    T H = rec[CR_PREF] * gauss<T>(rec[CR_LAM], rec[CR_NL2], c2);
     T l2c2 = T(2) * rec[CR_LAM] * c2;
     fp[0] = H * (T(1) + kqc * (l2c2 - T(D + 2)));
     if (NC == 2) fp[NC - 1] = H * rec[CR_NB] * (T(1) + kqc * (l2c2 - T(D)));
@@ -224,12 +283,12 @@ __device__ __forceinline__ void cell_slope(const DevCase<T> &dc, const T *__rest
                 T a2 = d1 * d1 + e2;
                 T num = a2 + T(2) * d1 * d2;
                 T den = a2 + d2 * (T(2) * d2 + d1);
-                T ph = den > T(0) ? num / den : T(1);
+                T ph = den > T(0) ? fdiv(num, den) : T(1);
                 phi[m] = ph < phi[m] ? ph : phi[m];
             }
         }
     }
-    const T dt = (T)dc.dt;
+    const T dt = dc.dtT;
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
         T ug = 0;
@@ -238,54 +297,81 @@ __device__ __forceinline__ void cell_slope(const DevCase<T> &dc, const T *__rest
         const T foot = -dt * ug;
         const T v = fi[m] + phi[m] * (dmin[m] + (foot < T(0) ? foot : T(0)));
         T s = phi[m];
-        if (v < T(0)) s *= fi[m] > T(0) ? fi[m] / (fi[m] - v) : T(0);
+        if (v < T(0)) s *= fi[m] > T(0) ? fdiv(fi[m], fi[m] - v) : T(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) g[m][d] *= s;
     }
 }
 
 // Interface flux of Eq. microscopicFlux with the distribution of Eq.
-// fullSolution integrated over the step (time integrals q1..q5 in the record):
-// F = u_n [q1 f_up + q2 u.grad f_up + q3 (g0 + g0+) + q4 u.grad g0 + q5 dg0/dt]
+// fullSolution integrated over the step (q1..q5):
+// F = u_n [q1 f_up + q2 u.grad f_up + H0(c) P(c)], the equilibrium part
+// q3 (g0 + g0+) + q4 u.grad g0 + q5 dg0/dt expanded into P (see XR_POLY).
+template <typename T, int D>
+__device__ __forceinline__ T poly_eval(const T *__restrict__ a, const T c[D], T c2)
+{
+    constexpr int NB = Poly<D>::NB;
+    T p = a[0];
+#pragma unroll
+    for (int e = 0; e < D; ++e) p += a[1 + e] * c[e];
+    int t = 1 + D;
+    T q = 0;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        T r = 0;
+#pragma unroll
+        for (int f = e; f < D; ++f) r += a[t + (e * (2 * D - e + 1)) / 2 + (f - e)] * c[f];
+        q += r * c[e];
+    }
+    p += q;
+    T g = 0;
+#pragma unroll
+    for (int e = 0; e < D; ++e) g += a[t + NB + e] * c[e];
+    return p + g * c2;
+}
+
+// copy a 16-byte aligned record of N values into registers with vector loads
+template <int N>
+__device__ __forceinline__ void load_rec(const float *__restrict__ p, float (&r)[N])
+{
+    static_assert(N % 4 == 0, "record length");
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + i);
+        r[4 * i] = v.x;
+        r[4 * i + 1] = v.y;
+        r[4 * i + 2] = v.z;
+        r[4 * i + 3] = v.w;
+    }
+}
+template <int N>
+__device__ __forceinline__ void load_rec(const double *__restrict__ p, double (&r)[N])
+{
+    static_assert(N % 2 == 0, "record length");
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + i);
+        r[2 * i] = v.x;
+        r[2 * i + 1] = v.y;
+    }
+}
+
 template <typename T, int D, int NC>
-__device__ __forceinline__ void interface_flux(const T *__restrict__ fr, const T u[3], T un,
+__device__ __forceinline__ void interface_flux(const T *__restrict__ xr, const T u[3], T un,
                                                const T fup[NC], const T ugf[NC], T F[NC])
 {
-    T c[D], c2 = 0, kqc = 0;
+    T c[D], c2 = 0;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-        c[d] = u[d] - fr[FR_U + d];
+        c[d] = u[d] - xr[XR_U + d];
         c2 += c[d] * c[d];
-        kqc += fr[FR_KQ + d] * c[d];
     }
-    const T lam = fr[FR_LAM];
-    const T H0 = fr[FR_PREF] * dexp(-lam * c2);
-    const T nb = fr[FR_NB], xb = fr[FR_XB];
-    const T l2c2 = T(2) * lam * c2;
-    const T hc2 = T(0.5) * c2;
-    T ua_h = 0, ua_b = 0;
+    const T H0 = xr[XR_PREF] * gauss<T>(xr[XR_LAM], xr[XR_NL2], c2);
+    const T q1 = xr[XR_Q1], q2 = xr[XR_Q2];
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-        const T *b = fr + FR_BETA + d * (D + 2);
-        T phi = b[0] + b[D + 1] * hc2;
-#pragma unroll
-        for (int e = 0; e < D; ++e) phi += b[1 + e] * c[e];
-        ua_h += u[d] * (phi + T(0.5) * b[D + 1] * nb);
-        if (NC == 2) ua_b += u[d] * (phi * nb + T(0.5) * b[D + 1] * xb);
-    }
-    const T *bA = fr + FR_BETA + D * (D + 2);
-    T phiA = bA[0] + bA[D + 1] * hc2;
-#pragma unroll
-    for (int e = 0; e < D; ++e) phiA += bA[1 + e] * c[e];
-    const T *qs = fr + FR_QS;
-    T sh_h = T(1) + kqc * (l2c2 - T(D + 2));
-    T At_h = phiA + T(0.5) * bA[D + 1] * nb;
-    F[0] = un * (qs[0] * fup[0] + qs[1] * ugf[0] + H0 * (qs[2] * sh_h + qs[3] * ua_h + qs[4] * At_h));
-    if (NC == 2) {
-        T sh_b = nb * (T(1) + kqc * (l2c2 - T(D)));
-        T At_b = phiA * nb + T(0.5) * bA[D + 1] * xb;
-        F[NC - 1] = un * (qs[0] * fup[NC - 1] + qs[1] * ugf[NC - 1] +
-                          H0 * (qs[2] * sh_b + qs[3] * ua_b + qs[4] * At_b));
+    for (int m = 0; m < NC; ++m) {
+        const T P = poly_eval<T, D>(xr + XR_POLY + m * Poly<D>::N, c, c2);
+        F[m] = un * (q1 * fup[m] + q2 * ugf[m] + H0 * P);
     }
 }
 

@@ -518,6 +518,9 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     dc.frL_d = c->upload(h.frL);
     dc.frR_d = c->upload(h.frR);
     dc.fn = c->upload(cast<T>(h.fn));
+    dc.frL = c->upload(cast<T>(h.frL));
+    dc.frR = c->upload(cast<T>(h.frR));
+    dc.dtT = (T)c->dt;
     dc.gface = c->upload(h.gface);
     dc.Wg = (double *)c->dalloc((size_t)std::max(c->G, 1) * M * sizeof(double));
     dc.grec = (T *)c->dalloc((size_t)std::max(c->G, 1) * ugks::GREC * sizeof(T));
@@ -544,6 +547,7 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     dc.krec = (T *)c->dalloc((size_t)c->C * ugks::CREC * sizeof(T));
     const size_t Fm = (size_t)std::max<int64_t>(c->F, 1);
     dc.frec = (T *)c->dalloc(Fm * ugks::FREC * sizeof(T));
+    dc.xrec = (T *)c->dalloc(Fm * ugks::XREC * sizeof(T));
     dc.fside = (T *)c->dalloc(Fm * 2 * ugks::GREC * sizeof(T));
     dc.fdW0 = (double *)c->dalloc(Fm * D * M * sizeof(double));
     dc.fq0 = (double *)c->dalloc(Fm * D * sizeof(double));
@@ -630,7 +634,7 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         const size_t esz = c->prec == UGKS_FP64 ? 8 : 4;
         // tiling: velocity tile of 32*TV, patch of P cells sized to shared memory
         c->vtile = params->vtile > 0 ? params->vtile : 32;
-        int P = params->patch_cells > 0 ? params->patch_cells : (c->prec == UGKS_FP64 ? 32 : 64);
+        int P = params->patch_cells > 0 ? params->patch_cells : (c->prec == UGKS_FP64 ? 32 : 48);
         Host h;
         int dev = 0;
         cuda_ok(cudaGetDevice(&dev), "cudaGetDevice");

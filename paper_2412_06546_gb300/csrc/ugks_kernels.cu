@@ -43,6 +43,8 @@ __device__ __forceinline__ Prim prim_of(const double *W, int D)
     return p;
 }
 
+constexpr double LOG2E = 1.4426950408889634073599246810018921;
+
 __device__ __forceinline__ double pref_of(double rho, double lam, int D)
 {
     double a = lam / 3.141592653589793238462643383279502884;
@@ -123,6 +125,7 @@ __global__ void k_init_f(DevCase<T> dc)
     rec[GR_LAM] = (T)p.lam;
     rec[GR_PREF] = (T)pref_of(p.rho, p.lam, D);
     rec[GR_NB] = (T)(dc.nxi / (2.0 * p.lam));
+    rec[GR_NL2] = (T)(-p.lam * LOG2E);
     const size_t rs = (size_t)NC * dc.nvp;
     for (int k = lane; k < dc.nvp; k += 32) {
         T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
@@ -184,6 +187,7 @@ __global__ void k_prep(DevCase<T> dc)
         for (int d = 0; d < 3; ++d) r[CR_KQ + d] = d < D ? (T)(kappa * dc.q[(size_t)c * D + d]) : T(0);
         r[CR_C] = (T)(0.5 * dc.dt / tau);
         r[CR_NB] = (T)(dc.nxi / (2.0 * p.lam));
+        r[CR_NL2] = (T)(-p.lam * LOG2E);
         return;
     }
     const int g = t - dc.C;
@@ -207,6 +211,7 @@ __global__ void k_prep(DevCase<T> dc)
     r[GR_LAM] = (T)p.lam;
     r[GR_PREF] = (T)pref_of(p.rho, p.lam, D);
     r[GR_NB] = (T)(dc.nxi / (2.0 * p.lam));
+    r[GR_NL2] = (T)(-p.lam * LOG2E);
 }
 
 // ------------------------------------------------------------ k_macro_grad
@@ -297,6 +302,7 @@ __device__ __forceinline__ void side_record(const double *Ws, double nxi, T *rec
     rec[GR_LAM] = (T)p.lam;
     rec[GR_PREF] = (T)pref_of(p.rho, p.lam, D);
     rec[GR_NB] = (T)(nxi / (2.0 * p.lam));
+    rec[GR_NL2] = (T)(-p.lam * LOG2E);
 }
 
 template <typename T, int D, int NC>
@@ -417,6 +423,7 @@ __global__ void k_face_fin1(DevCase<T> dc)
     for (int i = 0; i < 5; ++i) r[FR_QS + i] = (T)qs[i];
     r[FR_NB] = (T)(dc.nxi / (2.0 * p.lam));
     r[FR_XB] = (T)(dc.nxi * (dc.nxi + 2.0) / (4.0 * p.lam * p.lam));
+    r[FR_NL2] = (T)(-p.lam * LOG2E);
 }
 
 // number of unique entries of a symmetric (D+2)x(D+2) matrix
@@ -454,7 +461,7 @@ __global__ void k_face_sum2(DevCase<T> dc)
     const T *fr = dc.frec + (size_t)f * FREC;
     T U0[D];
     for (int d = 0; d < D; ++d) U0[d] = fr[FR_U + d];
-    const T lam = fr[FR_LAM], pref = fr[FR_PREF], nb = fr[FR_NB], xb = fr[FR_XB];
+    const T lam = fr[FR_LAM], pref = fr[FR_PREF], nb = fr[FR_NB], xb = fr[FR_XB], nl2 = fr[FR_NL2];
     T acc[S2];
     for (int i = 0; i < S2; ++i) acc[i] = 0;
     for (int k = lane; k < dc.nvp; k += 32) {
@@ -463,7 +470,7 @@ __global__ void k_face_sum2(DevCase<T> dc)
             c[d] = dc.u[d][k] - U0[d];
             c2 += c[d] * c[d];
         }
-        const T wH = dc.w[k] * pref * dexp(-lam * c2);
+        const T wH = dc.w[k] * pref * gauss<T>(lam, nl2, c2);
         T P[NS];
         psi_c_outer<T, D>(c, c2, nb, xb, P);
         for (int i = 0; i < NS; ++i) {
@@ -573,6 +580,64 @@ __global__ void k_face_fin2(DevCase<T> dc)
         for (int d = 0; d < D; ++d) xa[i] -= U0[d] * B[d * M + i];
     T *r = dc.frec + (size_t)f * FREC;
     for (int i = 0; i < (D + 1) * M; ++i) r[FR_BETA + i] = (T)B[i];
+
+    // Expand the equilibrium part of the interface distribution,
+    // q3 (g0 + g0+) + q4 u.grad g0 + q5 dg0/dt, into H0(c) P_m(c), c = u - U0:
+    //   h: sh = 1 + (kq.c)(2 lam |c|^2 - D - 2), slope terms of int (beta.psi_c) g0 dxi
+    //   b: sh = nb [1 + (kq.c)(2 lam |c|^2 - D)], slope terms of int xi^2 (beta.psi_c) g0 dxi
+    // with u_d = c_d + U0_d.
+    const double rho0 = pp[0], lam0 = pp[D + 1];
+    const double nb = dc.nxi / (2.0 * lam0), xb = dc.nxi * (dc.nxi + 2.0) / (4.0 * lam0 * lam0);
+    const double kappa = 4.0 * (1.0 - dc.Pr) * lam0 * lam0 / (5.0 * rho0);
+    double kq[D];
+    for (int d = 0; d < D; ++d) kq[d] = kappa * dc.fq0[(size_t)f * D + d];
+    double qs[5];
+    time_integrals(dc.dt, tau_of(dc, rho0, 1.0 / (2.0 * lam0)), qs);
+    T *x = dc.xrec + (size_t)f * XREC;
+    for (int d = 0; d < 3; ++d) x[XR_U + d] = d < D ? (T)U0[d] : T(0);
+    x[XR_PREF] = (T)pref_of(rho0, lam0, D);
+    x[XR_NL2] = (T)(-lam0 * LOG2E);
+    x[XR_LAM] = (T)lam0;
+    x[XR_Q1] = (T)qs[0];
+    x[XR_Q2] = (T)qs[1];
+    constexpr int NB = Poly<D>::NB, NP = Poly<D>::N;
+    for (int m = 0; m < NC; ++m) {
+        const double sm = m == 0 ? 1.0 : nb;            // scale of the b moments
+        const double xm = m == 0 ? nb : xb;             // xi^2 (resp. xi^4) factor of beta_E / 2
+        const double sh0 = m == 0 ? 1.0 : nb;
+        const double shl = m == 0 ? -(double)(D + 2) : -(double)D;
+        double a0 = qs[2] * sh0, a[D], Bq[D][D], gam[D];
+        for (int e = 0; e < D; ++e) {
+            a[e] = qs[2] * sh0 * shl * kq[e];
+            gam[e] = qs[2] * sh0 * 2.0 * lam0 * kq[e];
+            for (int g = 0; g < D; ++g) Bq[e][g] = 0.0;
+        }
+        double diag = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double *bd = B + d * M;                // beta^(d) in the psi_c basis
+            const double alpha = sm * bd[0] + 0.5 * bd[D + 1] * xm;
+            a0 += qs[3] * U0[d] * alpha;
+            a[d] += qs[3] * alpha;
+            for (int e = 0; e < D; ++e) {
+                a[e] += qs[3] * U0[d] * sm * bd[1 + e];
+                Bq[d][e] += qs[3] * sm * bd[1 + e];
+            }
+            diag += qs[3] * U0[d] * 0.5 * sm * bd[D + 1];
+            gam[d] += qs[3] * 0.5 * sm * bd[D + 1];
+        }
+        const double alphaA = sm * xa[0] + 0.5 * xa[D + 1] * xm;
+        a0 += qs[4] * alphaA;
+        for (int e = 0; e < D; ++e) a[e] += qs[4] * sm * xa[1 + e];
+        diag += qs[4] * 0.5 * sm * xa[D + 1];
+        T *pm = x + XR_POLY + m * NP;
+        pm[0] = (T)a0;
+        for (int e = 0; e < D; ++e) pm[1 + e] = (T)a[e];
+        int t = 1 + D;
+        for (int e = 0; e < D; ++e)
+            for (int g = e; g < D; ++g)
+                pm[t++] = (T)(e == g ? Bq[e][e] + diag : Bq[e][g] + Bq[g][e]);
+        for (int e = 0; e < D; ++e) pm[1 + D + NB + e] = (T)gam[e];
+    }
 }
 
 // ------------------------------------------------------------ walls
@@ -580,10 +645,11 @@ __global__ void k_face_fin2(DevCase<T> dc)
 // carry the interior reconstruction transported freely over the step,
 // incoming ones the wall Maxwellian.
 template <typename T, int D, int NC>
-__global__ void k_wall_sum(DevCase<T> dc)
+__global__ void __launch_bounds__(256) k_wall_sum(DevCase<T> dc)
 {
-    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+    __shared__ T red[2][8];
+    const int s = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (s >= dc.NW) return;
     const int f = dc.wface[s];
     const int c = dc.fL[f];
@@ -595,15 +661,17 @@ __global__ void k_wall_sum(DevCase<T> dc)
     wr[GR_LAM] = (T)lw;
     wr[GR_PREF] = (T)pref_of(1.0, lw, D);
     wr[GR_NB] = (T)(dc.nxi / (2.0 * lw));
+    wr[GR_NL2] = (T)(-lw * LOG2E);
+    wr[GREC - 1] = T(0);
     T n[D], r[D];
     for (int d = 0; d < D; ++d) {
         n[d] = dc.fn[(size_t)f * D + d];
-        r[d] = (T)dc.frL_d[(size_t)f * D + d];
+        r[d] = dc.frL[(size_t)f * D + d];
     }
-    const T hdt = T(0.5 * dc.dt);
+    const T hdt = T(0.5) * dc.dtT;
     const size_t rs = (size_t)NC * dc.nvp;
     T num = 0, den = 0;
-    for (int k = lane; k < dc.nvp; k += 32) {
+    for (int k = threadIdx.x; k < dc.nvp; k += blockDim.x) {
         T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
         T un = normal_velocity<T, D>(u, n);
         if (un > T(0)) {
@@ -622,7 +690,17 @@ __global__ void k_wall_sum(DevCase<T> dc)
     num = warp_sum(num);
     den = warp_sum(den);
     if (lane == 0) {
-        const double rw = -(double)num / (double)den;
+        red[0][warp] = num;
+        red[1][warp] = den;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += (double)red[0][w];
+            b += (double)red[1][w];
+        }
+        const double rw = -a / b;
         dc.rho_w[s] = rw;
         T *w = dc.wrec + (size_t)s * GREC;
         for (int i = 0; i < GREC; ++i) w[i] = wr[i];
@@ -679,8 +757,8 @@ __global__ void __launch_bounds__(256) k_gather(DevCase<T> dc)
     __syncthreads();
 
     // ---- phase B: fluxes, stage 1, moments (Alg. 1 lines 6-8, 10)
-    const T dt = (T)dc.dt;
-    const T hdt2 = T(0.5 * dc.dt * dc.dt);
+    const T dt = dc.dtT;
+    const T hdt2 = T(0.5) * dc.dtT * dc.dtT;
     for (int s = warp; s < npc; s += nwarps) {
         const int c = cb + s;
         T R[TV][NC];
@@ -728,14 +806,15 @@ __global__ void __launch_bounds__(256) k_gather(DevCase<T> dc)
                     for (int m = 0; m < NC; ++m) R[j][m] += coef * F[m];
                 }
             } else {
-                const T *fr = dc.frec + (size_t)fid * FREC;
+                T fr[XREC];
+                load_rec<XREC>(dc.xrec + (size_t)fid * XREC, fr);
                 const int sL = dc.cf_sL[e], sR = dc.cf_sR[e];
                 const int cL = dc.fL[fid], cR = dc.fR[fid];
                 T rL[D], rR[D];
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
-                    rL[d] = (T)dc.frL_d[(size_t)fid * D + d];
-                    rR[d] = typ == FT_FARFIELD ? T(0) : (T)dc.frR_d[(size_t)fid * D + d];
+                    rL[d] = dc.frL[(size_t)fid * D + d];
+                    rR[d] = typ == FT_FARFIELD ? T(0) : dc.frR[(size_t)fid * D + d];
                 }
 #pragma unroll
                 for (int j = 0; j < TV; ++j) {
@@ -800,11 +879,14 @@ __global__ void __launch_bounds__(256) k_gather(DevCase<T> dc)
             for (int d = 0; d < D; ++d) mom[1 + d] += u[j][d] * wr0;
             mom[D + 1] += T(0.5) * (u2 * wr0 + (NC == 2 ? wk * R[j][NC - 1] : T(0)));
         }
+        constexpr int NR = M <= 4 ? 4 : 8;
+        T red[NR];
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-            const T sm = warp_sum(mom[i]);
-            if (lane == 0) dc.dW_part[((size_t)c * dc.n_vt + vt) * M + i] = (double)sm;
-        }
+        for (int i = 0; i < NR; ++i) red[i] = i < M ? mom[i] : T(0);
+        const T sm = warp_transpose_sum<T, NR>(red);
+        const int vi = lane >> (NR == 4 ? 3 : 2);
+        if ((lane & (NR == 4 ? 7 : 3)) == 0 && vi < M)
+            dc.dW_part[((size_t)c * dc.n_vt + vt) * M + vi] = (double)sm;
     }
 }
 
@@ -837,6 +919,7 @@ __global__ void __launch_bounds__(256) k_update_W(DevCase<T> dc)
         for (int d = 0; d < 3; ++d) r[CR_KQ + d] = d < D ? (T)(kappa * dc.q[(size_t)c * D + d]) : T(0);
         r[CR_C] = (T)(0.5 * dc.dt / tau);
         r[CR_NB] = (T)(dc.nxi / (2.0 * p.lam));
+        r[CR_NL2] = (T)(-p.lam * LOG2E);
     }
     // deterministic block partials of the residual
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -877,9 +960,16 @@ __global__ void k_residual(const double *res_part, int nblocks, double *res)
 }
 
 // ------------------------------------------------------------ stage 2
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+
+// 4 consecutive velocities per lane (rows are padded to a multiple of 32, so
+// every row start is 16-byte aligned for FP32 and 32-byte aligned for FP64)
 template <typename T, int D, int NC>
 __global__ void k_collide(DevCase<T> dc)
 {
+    using V4 = typename Vec4<T>::type;
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (c >= dc.C) return;
@@ -891,23 +981,43 @@ __global__ void k_collide(DevCase<T> dc)
     const size_t rs = (size_t)NC * dc.nvp;
     T acc[D];
     for (int d = 0; d < D; ++d) acc[d] = 0;
-    for (int k = lane; k < dc.nvp; k += 32) {
-        T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
-        T fp[NC];
-        shakhov_fplus<T, D, NC>(kr, u, fp);
-        T fn[NC];
+    for (int k0 = 4 * lane; k0 < dc.nvp; k0 += 128) {
+        T ft[NC][4], fn[NC][4];
+#pragma unroll
         for (int m = 0; m < NC; ++m) {
-            const size_t o = (size_t)c * rs + (size_t)m * dc.nvp + k;
-            fn[m] = (dc.f_nxt[o] + cc * fp[m]) * inv;
-            dc.f_cur[o] = fn[m];
+            const V4 v = *reinterpret_cast<const V4 *>(dc.f_nxt + (size_t)c * rs + (size_t)m * dc.nvp + k0);
+            ft[m][0] = v.x;
+            ft[m][1] = v.y;
+            ft[m][2] = v.z;
+            ft[m][3] = v.w;
         }
-        T cv[D], c2 = 0;
-        for (int d = 0; d < D; ++d) {
-            cv[d] = u[d] - U[d];
-            c2 += cv[d] * cv[d];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = k0 + j;
+            T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
+            T fp[NC];
+            shakhov_fplus<T, D, NC>(kr, u, fp);
+#pragma unroll
+            for (int m = 0; m < NC; ++m) fn[m][j] = (ft[m][j] + cc * fp[m]) * inv;
+            T cv[D], c2 = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                cv[d] = u[d] - U[d];
+                c2 += cv[d] * cv[d];
+            }
+            const T we = dc.w[k] * (c2 * fn[0][j] + (NC == 2 ? fn[NC - 1][j] : T(0)));
+#pragma unroll
+            for (int d = 0; d < D; ++d) acc[d] += cv[d] * we;
         }
-        const T we = dc.w[k] * (c2 * fn[0] + (NC == 2 ? fn[NC - 1] : T(0)));
-        for (int d = 0; d < D; ++d) acc[d] += cv[d] * we;
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            V4 v;
+            v.x = fn[m][0];
+            v.y = fn[m][1];
+            v.z = fn[m][2];
+            v.w = fn[m][3];
+            *reinterpret_cast<V4 *>(dc.f_cur + (size_t)c * rs + (size_t)m * dc.nvp + k0) = v;
+        }
     }
     for (int d = 0; d < D; ++d) {
         T s = warp_sum(acc[d]);
@@ -1020,7 +1130,7 @@ static cudaError_t step_dn(const DevCase<T> &dc, const StepConfig &cfg, cudaStre
         k_face_fin2<T, D, NC><<<cdiv(F, 64), 64, 0, st>>>(dc);
     }
     mark(2);
-    if (dc.NW > 0) k_wall_sum<T, D, NC><<<cdiv(dc.NW, 8), 256, 0, st>>>(dc);
+    if (dc.NW > 0) k_wall_sum<T, D, NC><<<dc.NW, 256, 0, st>>>(dc);
     mark(3);
     cudaError_t e;
     switch (dc.vtile / 32) {
