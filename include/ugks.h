@@ -98,7 +98,8 @@ typedef struct {
     double inf_rho, inf_U[3], inf_T; /* far-field state */
     int32_t precision;      /* UGKS_FP64 or UGKS_FP32 */
     const double *prim_init;/* [n_cells][dim+2] initial (rho, U, T), or NULL: far-field state */
-    int32_t patch_cells;    /* gather tiling: cells per patch (0: automatic) */
+    int32_t patch_cells;    /* gather tiling: cells per patch (0: autotuned by timing the gather
+                               kernel on this case, cached per case shape) */
     int32_t vtile;          /* gather tiling: velocities per tile, 32, 64 or 128 (0: automatic) */
 } ugks_params;
 
@@ -166,6 +167,20 @@ ugks_status ugks_set_state(ugks_case *c, const double *f, const double *W);
  * *steps.  Not part of the method; used by the benchmark. */
 ugks_status ugks_profile_begin(ugks_case *c, int32_t max_steps);
 ugks_status ugks_profile_end(ugks_case *c, double *ms, int32_t n, int32_t *steps);
+
+/* Batched stepping of several cases (one GPU).  The cases must share the
+ * dimension, precision and velocity tile.  Each batch step runs every case's
+ * gather pass in one persistent kernel that walks a (case, patch, velocity
+ * tile) work list, and the other kernels of every case on parallel graph
+ * branches; the whole step is captured once as a CUDA graph on `stream`
+ * (cudaStream_t, NULL: a stream of the batch's own) and replayed.  Results
+ * are bit-identical to stepping each case alone with ugks_step.  The cases
+ * stay owned by the caller and must outlive the batch; ugks_batch_step
+ * advances each case's step counter. */
+typedef struct ugks_batch ugks_batch;
+ugks_status ugks_batch_create(ugks_case *const *cases, int32_t n, void *stream, ugks_batch **out);
+ugks_status ugks_batch_step(ugks_batch *b, int32_t nsteps);
+void ugks_batch_destroy(ugks_batch *b);
 
 /* Sizes and tiling of a case. */
 ugks_status ugks_info(const ugks_case *c, ugks_info_t *info);

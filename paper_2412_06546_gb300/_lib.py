@@ -83,6 +83,9 @@ EXPORTS = {
     "ugks_profile_end": (ct.c_int, [ct.c_void_p, D_P, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "ugks_residual_noalloc": (ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p,
                                          ct.c_void_p]),
+    "ugks_batch_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    "ugks_batch_step": (ct.c_int, [ct.c_void_p, ct.c_int32]),
+    "ugks_batch_destroy": (None, [ct.c_void_p]),
     "ugks_destroy": (None, [ct.c_void_p]),
     "ugks_last_error": (ct.c_char_p, []),
 }
@@ -254,3 +257,31 @@ class Case:
         n = ct.c_int32()
         check(load().ugks_profile_end(self._h, _p(ms), len(ms), ct.byref(n)))
         return dict(zip(self.GROUPS, ms)), n.value
+
+
+class Batch:
+    """Several cases stepped together: one persistent gather launch over a
+    (case, patch, velocity tile) work list per step, the whole step captured
+    once as a CUDA graph (``ugks_batch_*``)."""
+
+    def __init__(self, cases, stream=None):
+        L = load()
+        self.cases = list(cases)
+        arr = (ct.c_void_p * len(self.cases))(*[c._h.value for c in self.cases])
+        h = ct.c_void_p()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        check(L.ugks_batch_create(arr, len(self.cases), ct.c_void_p(stream or 0), ct.byref(h)))
+        self._h = h
+        self.stream = stream
+
+    def step(self, n=1):
+        check(load().ugks_batch_step(self._h, int(n)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ugks_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close

@@ -101,6 +101,9 @@ struct DevCase {
     double *dW_part;              // [C][n_vt][D+2]
     double *res_part;             // [n_res_blocks][2(D+2)]
     int *flags;                   // [1] numeric failure flag
+    // tensor-product velocity grid (sep = 1): axes and 1-D weights per dimension
+    int sep, cart_n[3];
+    const T *axis[3], *axw[3];
     // gather tiling
     int P, n_patches, n_vt, vtile;
     const int *ring_ptr, *ring_cells;

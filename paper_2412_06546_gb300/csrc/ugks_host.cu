@@ -11,7 +11,9 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <stdexcept>
 #include <string>
@@ -237,6 +239,8 @@ bool invert_small(int D, const double *A, double *Ainv)
     return true;
 }
 
+void build_patches(Host &h, int C, int P);
+
 void preprocess(const ugks_mesh *m, const ugks_params *p, int P, Host &h)
 {
     const int D = m->dim;
@@ -387,7 +391,17 @@ void preprocess(const ugks_mesh *m, const ugks_params *p, int P, Host &h)
         h.eps2[c] = Kh * Kh * Kh;
     }
 
-    // ---- gather patches: P consecutive cells + their face neighbours (ring)
+    build_patches(h, C, P);
+}
+
+// gather patches: P consecutive cells (Morton order) and their face neighbours
+// (ring); slot indices of every face entry's owner / neighbour in its patch
+void build_patches(Host &h, int C, int P)
+{
+    const int ncf = h.cf_ptr[C];
+    h.ring_ptr.clear();
+    h.ring_cells.clear();
+    h.max_slope = 0;
     const int np = (C + P - 1) / P;
     h.ring_ptr.assign(np + 1, 0);
     h.cf_sL.assign(ncf, -1);
@@ -459,6 +473,58 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
         for (int64_t k = 0; k < c->Nv; ++k) ud[k] = v->u[k * D + d];
         dc.ud[d] = c->upload(ud);
         dc.u[d] = c->upload(cast<T>(ud));
+    }
+    // tensor-product grid: u_k = (x_i, y_j[, z_l]), k = i + nx (j + ny l), and
+    // w_k = wx_i wy_j [wz_l]; verified exactly for the axes and to 1e-14 for the
+    // weights, else the general per-velocity face sums are used
+    dc.sep = 0;
+    for (int d = 0; d < 3; ++d) {
+        dc.cart_n[d] = 0;
+        dc.axis[d] = dc.axw[d] = nullptr;
+    }
+    {
+        int64_t prod = 1;
+        bool ok = true;
+        for (int d = 0; d < D; ++d) {
+            ok = ok && v->cart_n[d] > 1;
+            prod *= std::max(v->cart_n[d], 1);
+        }
+        ok = ok && prod == c->Nv;
+        if (ok) {
+            const int nx = v->cart_n[0], ny = v->cart_n[1], nz = D == 3 ? v->cart_n[2] : 1;
+            std::vector<std::vector<double>> ax(D), aw(D);
+            auto kidx = [&](int i, int j, int l) { return (int64_t)i + (int64_t)nx * (j + (int64_t)ny * l); };
+            const int nn[3] = {nx, ny, nz};
+            for (int d = 0; d < D; ++d) {
+                for (int i = 0; i < nn[d]; ++i) {
+                    int ijk[3] = {0, 0, 0};
+                    ijk[d] = i;
+                    const int64_t k = kidx(ijk[0], ijk[1], ijk[2]);
+                    ax[d].push_back(v->u[k * D + d]);
+                    aw[d].push_back(d == 0 ? v->w[k] : v->w[k] / v->w[0]);
+                }
+            }
+            for (int l = 0; l < nz && ok; ++l)
+                for (int j = 0; j < ny && ok; ++j)
+                    for (int i = 0; i < nx && ok; ++i) {
+                        const int64_t k = kidx(i, j, l);
+                        const int ijk[3] = {i, j, l};
+                        double wp = 1.0;
+                        for (int d = 0; d < D; ++d) {
+                            ok = ok && v->u[k * D + d] == ax[d][ijk[d]];
+                            wp *= aw[d][ijk[d]];
+                        }
+                        ok = ok && std::fabs(wp - v->w[k]) <= 1e-14 * std::fabs(v->w[k]) + 1e-300;
+                    }
+            if (ok) {
+                dc.sep = 1;
+                for (int d = 0; d < D; ++d) {
+                    dc.cart_n[d] = nn[d];
+                    dc.axis[d] = c->upload(cast<T>(ax[d]));
+                    dc.axw[d] = c->upload(cast<T>(aw[d]));
+                }
+            }
+        }
     }
     std::vector<double> wd(c->nvp, 0.0);
     for (int64_t k = 0; k < c->Nv; ++k) wd[k] = v->w[k];
@@ -570,6 +636,82 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
 }  // namespace
 
 namespace {
+
+// Autotuner of the gather tiling: the patch size is chosen by timing the gather
+// kernel itself on this case (it writes only f~ and scratch, so the state is
+// untouched), and the choice is cached per (dimension, precision, velocity
+// tile, velocity count, mesh-size bucket) for later cases of the same shape.
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune_cache;
+
+template <typename T>
+void set_patches(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, size_t smem)
+{
+    c->P = P;
+    c->n_patches = (int)((c->C + P - 1) / P);
+    c->cfg.smem = smem;
+    dc.P = P;
+    dc.n_patches = c->n_patches;
+    dc.ring_ptr = c->upload(h.ring_ptr);
+    dc.ring_cells = c->upload(h.ring_cells);
+    dc.cf_sL = c->upload(h.cf_sL);
+    dc.cf_sR = c->upload(h.cf_sR);
+}
+
+template <typename T>
+void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max)
+{
+    const size_t esz = sizeof(T);
+    char key[160];
+    snprintf(key, sizeof(key), "D%d_nc%d_p%d_vt%d_nv%lld_c%d", c->D, c->NC, c->prec, c->vtile, (long long)c->Nv,
+             (int)std::lround(std::log2((double)c->C)));
+    int best = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) best = it->second;
+    }
+    const int C = (int)c->C;
+    auto smem_of = [&](const Host &hh) { return (size_t)hh.max_slope * c->NC * c->D * c->vtile * esz; };
+    if (best == 0) {
+        const std::vector<int> cand = c->prec == UGKS_FP64 ? std::vector<int>{16, 24, 32, 48}
+                                                           : std::vector<int>{32, 48, 64, 96};
+        cuda_ok(ugks::launch_pre_gather(dc, c->stream), "autotune prep");
+        cudaEvent_t e0, e1;
+        cuda_ok(cudaEventCreate(&e0), "event");
+        cuda_ok(cudaEventCreate(&e1), "event");
+        float best_ms = 0.f;
+        for (int P : cand) {
+            if (P > C && P != cand.front()) continue;
+            build_patches(h, C, P);
+            const size_t smem = smem_of(h);
+            if (smem > (size_t)smem_max) continue;
+            set_patches(c, dc, h, P, smem);
+            cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
+            cuda_ok(cudaEventRecord(e0, c->stream), "event");
+            for (int r = 0; r < 2; ++r) cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
+            cuda_ok(cudaEventRecord(e1, c->stream), "event");
+            cuda_ok(cudaEventSynchronize(e1), "event");
+            float ms = 0.f;
+            cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "event");
+            if (best == 0 || ms < best_ms) {
+                best = P;
+                best_ms = ms;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (best == 0) return;                       // keep the default tiling
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = best;
+    }
+    if (best != c->P) {
+        build_patches(h, C, best);
+        const size_t smem = smem_of(h);
+        if (smem <= (size_t)smem_max) set_patches(c, dc, h, best, smem);
+    }
+}
+
 ugks_status guard(const std::function<void()> &fn)
 {
     try {
@@ -677,9 +819,11 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         if (c->prec == UGKS_FP64) {
             fill_case<double>(c.get(), c->d64, mesh, vgrid, params, h);
             cuda_ok(ugks::launch_init(c->d64, c->stream), "init");
+            if (params->patch_cells == 0) autotune<double>(c.get(), c->d64, h, smem_max);
         } else {
             fill_case<float>(c.get(), c->d32, mesh, vgrid, params, h);
             cuda_ok(ugks::launch_init(c->d32, c->stream), "init");
+            if (params->patch_cells == 0) autotune<float>(c.get(), c->d32, h, smem_max);
         }
         cuda_ok(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "create sync");
     });
@@ -881,6 +1025,203 @@ ugks_status ugks_info(const ugks_case *c, ugks_info_t *info)
         info->vtile = c->vtile;
         info->kernel_launches_per_step = 5 + (c->F > 0 ? 5 : 0) + (c->NW > 0 ? 1 : 0);
     });
+}
+
+}  // extern "C"
+
+struct ugks_batch {
+    std::vector<ugks_case *> cases;
+    int D = 0, prec = 0, vtile = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *dcases = nullptr;         // device array of DevCase<T>
+    int4 *work = nullptr;
+    int nwork = 0, grid = 0;
+    size_t smem = 0;
+    static constexpr int NB = 8;    // parallel branches for the per-case kernels
+    cudaStream_t br[NB] = {};
+    cudaEvent_t fork = nullptr, fork2 = nullptr, join[NB] = {}, join2[NB] = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> case_ev;   // orders each case's stream with the batch stream
+    cudaEvent_t done = nullptr;
+};
+
+namespace {
+
+template <typename T>
+ugks::DevCase<T> &dc_of(ugks_case *c);
+template <>
+ugks::DevCase<double> &dc_of<double>(ugks_case *c) { return c->d64; }
+template <>
+ugks::DevCase<float> &dc_of<float>(ugks_case *c) { return c->d32; }
+
+template <typename T>
+void batch_build(ugks_batch *b)
+{
+    const int n = (int)b->cases.size();
+    std::vector<ugks::DevCase<T>> h(n);
+    size_t smem = 0;
+    std::vector<int4> work;
+    int max_vt = 0;
+    for (int i = 0; i < n; ++i) {
+        h[i] = dc_of<T>(b->cases[i]);
+        smem = std::max(smem, b->cases[i]->cfg.smem);
+        max_vt = std::max(max_vt, b->cases[i]->n_vt);
+    }
+    // velocity tile outer, case, then patch innermost: consecutive CTAs work on
+    // neighbouring patches of one case and tile, as in the single-case grid
+    for (int vt = 0; vt < max_vt; ++vt)
+        for (int i = 0; i < n; ++i) {
+            if (vt >= b->cases[i]->n_vt) continue;
+            for (int pi = 0; pi < b->cases[i]->n_patches; ++pi) work.push_back(make_int4(i, pi, vt, 0));
+        }
+    cuda_ok(cudaMalloc(&b->dcases, sizeof(ugks::DevCase<T>) * n), "batch alloc");
+    cuda_ok(cudaMemcpy(b->dcases, h.data(), sizeof(ugks::DevCase<T>) * n, cudaMemcpyHostToDevice), "batch upload");
+    cuda_ok(cudaMalloc((void **)&b->work, sizeof(int4) * std::max<size_t>(1, work.size())), "batch alloc");
+    cuda_ok(cudaMemcpy(b->work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice), "batch upload");
+    b->nwork = (int)work.size();
+    b->smem = smem;
+    b->grid = std::min(b->nwork, ugks::gather_resident_ctas<T>(b->D, b->vtile, smem));
+}
+
+template <typename T>
+void batch_capture(ugks_batch *b)
+{
+    cudaStream_t st = b->stream;
+    cuda_ok(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cuda_ok(cudaEventRecord(b->fork, st), "fork");
+    for (int k = 0; k < ugks_batch::NB; ++k) cuda_ok(cudaStreamWaitEvent(b->br[k], b->fork, 0), "fork wait");
+    for (size_t i = 0; i < b->cases.size(); ++i)
+        cuda_ok(ugks::launch_pre_gather(dc_of<T>(b->cases[i]), b->br[i % ugks_batch::NB]), "pre-gather");
+    for (int k = 0; k < ugks_batch::NB; ++k) {
+        cuda_ok(cudaEventRecord(b->join[k], b->br[k]), "join");
+        cuda_ok(cudaStreamWaitEvent(st, b->join[k], 0), "join wait");
+    }
+    cuda_ok(ugks::launch_gather_batch<T>(b->D, b->vtile, (const ugks::DevCase<T> *)b->dcases, b->work, b->nwork,
+                                         b->grid, b->smem, st),
+            "batched gather");
+    cuda_ok(cudaEventRecord(b->fork2, st), "fork");
+    for (int k = 0; k < ugks_batch::NB; ++k) cuda_ok(cudaStreamWaitEvent(b->br[k], b->fork2, 0), "fork wait");
+    for (size_t i = 0; i < b->cases.size(); ++i) {
+        ugks_case *c = b->cases[i];
+        cuda_ok(ugks::launch_post_gather(dc_of<T>(c), c->cfg, b->br[i % ugks_batch::NB]), "post-gather");
+    }
+    for (int k = 0; k < ugks_batch::NB; ++k) {
+        cuda_ok(cudaEventRecord(b->join2[k], b->br[k]), "join");
+        cuda_ok(cudaStreamWaitEvent(st, b->join2[k], 0), "join wait");
+    }
+    cuda_ok(cudaStreamEndCapture(st, &b->graph), "end capture");
+    cuda_ok(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
+}
+
+void batch_free(ugks_batch *b)
+{
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->dcases) cudaFree(b->dcases);
+    if (b->work) cudaFree(b->work);
+    for (int k = 0; k < ugks_batch::NB; ++k) {
+        if (b->br[k]) cudaStreamDestroy(b->br[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+        if (b->join2[k]) cudaEventDestroy(b->join2[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->fork2) cudaEventDestroy(b->fork2);
+    for (auto e : b->case_ev)
+        if (e) cudaEventDestroy(e);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+ugks_status ugks_batch_create(ugks_case *const *cases, int32_t n, void *stream, ugks_batch **out)
+{
+    if (!out) {
+        g_err = "out must not be NULL";
+        return UGKS_EINVAL;
+    }
+    *out = nullptr;
+    std::unique_ptr<ugks_batch> b(new ugks_batch());
+    ugks_status st = guard([&] {
+        if (!cases || n <= 0) fail(UGKS_EINVAL, "a batch needs at least one case");
+        for (int i = 0; i < n; ++i) {
+            if (!cases[i]) fail(UGKS_EINVAL, "case %d is NULL", i);
+            if (cases[i]->D != cases[0]->D || cases[i]->prec != cases[0]->prec || cases[i]->vtile != cases[0]->vtile)
+                fail(UGKS_EINVAL, "case %d differs from case 0 in dimension, precision or velocity tile", i);
+            for (int j = 0; j < i; ++j)
+                if (cases[j] == cases[i]) fail(UGKS_EINVAL, "case %d appears twice", i);
+            b->cases.push_back(cases[i]);
+        }
+        b->D = cases[0]->D;
+        b->prec = cases[0]->prec;
+        b->vtile = cases[0]->vtile;
+        if (stream) {
+            b->stream = (cudaStream_t)stream;
+        } else {
+            cuda_ok(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "stream");
+            b->own_stream = true;
+        }
+        for (int k = 0; k < ugks_batch::NB; ++k) {
+            cuda_ok(cudaStreamCreateWithFlags(&b->br[k], cudaStreamNonBlocking), "stream");
+            cuda_ok(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming), "event");
+            cuda_ok(cudaEventCreateWithFlags(&b->join2[k], cudaEventDisableTiming), "event");
+        }
+        cuda_ok(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
+        cuda_ok(cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming), "event");
+        cuda_ok(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming), "event");
+        b->case_ev.assign(b->cases.size(), nullptr);
+        for (auto &e : b->case_ev) cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        // the cases' own streams must have finished their queued work
+        for (auto *c : b->cases) cuda_ok(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "sync");
+        if (b->prec == UGKS_FP64) batch_build<double>(b.get());
+        else batch_build<float>(b.get());
+    });
+    if (st != UGKS_OK) {
+        std::string keep = g_err;
+        batch_free(b.get());
+        g_err = keep;
+        return st;
+    }
+    *out = b.release();
+    return UGKS_OK;
+}
+
+ugks_status ugks_batch_step(ugks_batch *b, int32_t nsteps)
+{
+    return guard([&] {
+        if (!b) fail(UGKS_EINVAL, "batch is NULL");
+        if (nsteps < 0) fail(UGKS_EINVAL, "nsteps must be >= 0");
+        if (nsteps == 0) return;
+        if (!b->exec) {
+            if (b->prec == UGKS_FP64) batch_capture<double>(b);
+            else batch_capture<float>(b);
+        }
+        // work queued on the cases' own streams comes first, and later calls
+        // on a case (moments, state I/O, ugks_step) wait for the batch
+        for (size_t i = 0; i < b->cases.size(); ++i) {
+            cuda_ok(cudaEventRecord(b->case_ev[i], b->cases[i]->stream), "order");
+            cuda_ok(cudaStreamWaitEvent(b->stream, b->case_ev[i], 0), "order");
+        }
+        for (int32_t s = 0; s < nsteps; ++s) cuda_ok(cudaGraphLaunch(b->exec, b->stream), "graph launch");
+        cuda_ok(cudaEventRecord(b->done, b->stream), "order");
+        for (auto *c : b->cases) {
+            cuda_ok(cudaStreamWaitEvent(c->stream, b->done, 0), "order");
+            c->step += nsteps;
+            c->stepped = true;
+        }
+    });
+}
+
+void ugks_batch_destroy(ugks_batch *b)
+{
+    if (!b) return;
+    batch_free(b);
+    delete b;
 }
 
 void ugks_destroy(ugks_case *c)

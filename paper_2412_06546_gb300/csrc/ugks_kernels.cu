@@ -18,6 +18,7 @@
 #include "ugks_device.cuh"
 #include "ugks_kernels.h"
 
+#include <algorithm>
 #include <cmath>
 
 namespace ugks {
@@ -485,6 +486,97 @@ __global__ void k_face_sum2(DevCase<T> dc)
     }
 }
 
+// The same sums as k_face_sum2 on a tensor-product velocity grid, where
+// u_k = (x_i, y_j[, z_l]) and w_k = wx_i wy_j [wz_l]: every moment of g0 the slope
+// systems need is sum_k w_k H0(u_k) c^alpha = pref0 prod_d m_d[alpha_d] with the
+// 1-D moments m_d[p] = sum_i w_{d,i} exp(-lam0 c_{d,i}^2) c_{d,i}^p, p <= 5.
+// This kernel reduces the 1-D moments (warp per face); k_face_fin2 forms the
+// products (thread per face, FP64).
+template <typename T, int D, int NC>
+__global__ void k_face_sum2_sep(DevCase<T> dc)
+{
+    const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    constexpr int NS = Sym<D>::N;
+    if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
+    const T *fr = dc.frec + (size_t)f * FREC;
+    const T lam = fr[FR_LAM], nl2 = fr[FR_NL2];
+    double *out = dc.fsum2 + (size_t)f * NS * (D + 1);
+    for (int d = 0; d < D; ++d) {
+        const T U0 = fr[FR_U + d];
+        T acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = lane; i < dc.cart_n[d]; i += 32) {
+            const T c = dc.axis[d][i] - U0;
+            T v = dc.axw[d][i] * gauss<T>(lam, nl2, c * c);
+#pragma unroll
+            for (int pw = 0; pw < 6; ++pw) {
+                acc[pw] += v;
+                v *= c;
+            }
+        }
+#pragma unroll
+        for (int pw = 0; pw < 6; ++pw) {
+            const T sm = warp_sum(acc[pw]);
+            if (lane == pw) out[d * 6 + pw] = (double)sm;
+        }
+    }
+}
+
+// M_c and T_c,d of k_face_sum2 from the 1-D moments m[d][0..5] (tensor grids)
+template <int D>
+__device__ void sep_moments(const double m[D][6], double pref, double nb, double xb, double *S)
+{
+    constexpr int NS = Sym<D>::N;
+    constexpr int M = D + 2;
+    auto Q = [&](const int *a) {
+        double r = pref;
+        for (int d = 0; d < D; ++d) r *= m[d][a[d]];
+        return r;
+    };
+    for (int t = -1; t < D; ++t) {          // t = -1: M_c; t = d: T_c,d (extra factor c_d)
+        int base[3] = {0, 0, 0};
+        if (t >= 0) base[t] = 1;
+        int idx = 0;
+        for (int i = 0; i < M; ++i)
+            for (int j = i; j < M; ++j) {
+                double val;
+                int a[3] = {base[0], base[1], base[2]};
+                const bool iE = i == M - 1, jE = j == M - 1;
+                if (!iE && !jE) {
+                    if (i > 0) a[i - 1]++;
+                    if (j > 0) a[j - 1]++;
+                    val = Q(a);
+                } else if (!iE || !jE) {
+                    // psi_o (|c|^2 + xi^2)/2 with psi_o = 1 or c_(o-1)
+                    const int o = iE ? j : i;
+                    if (o > 0) a[o - 1]++;
+                    double s2 = 0.0;
+                    for (int e = 0; e < D; ++e) {
+                        int b[3] = {a[0], a[1], a[2]};
+                        b[e] += 2;
+                        s2 += Q(b);
+                    }
+                    val = 0.5 * (s2 + nb * Q(a));
+                } else {
+                    double s4 = 0.0, s2 = 0.0;
+                    for (int e = 0; e < D; ++e) {
+                        int b[3] = {a[0], a[1], a[2]};
+                        b[e] += 2;
+                        s2 += Q(b);
+                        for (int g = 0; g < D; ++g) {
+                            int c4[3] = {b[0], b[1], b[2]};
+                            c4[g] += 2;
+                            s4 += Q(c4);
+                        }
+                    }
+                    val = 0.25 * (s4 + 2.0 * nb * s2 + xb * Q(a));
+                }
+                S[NS * (t + 1) + idx] = val;
+                ++idx;
+            }
+    }
+}
+
 // Cholesky solve of the SPD system A x = b (n <= 5), A overwritten
 __device__ void chol_solve(int n, double *A, double *b, int nrhs, int ldb)
 {
@@ -524,7 +616,18 @@ __global__ void k_face_fin2(DevCase<T> dc)
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     constexpr int M = D + 2, NS = Sym<D>::N, S2 = NS * (D + 1);
     if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
+    double Ssep[S2];
     const double *S = dc.fsum2 + (size_t)f * S2;
+    if (dc.sep) {
+        double m1[D][6];
+        for (int d = 0; d < D; ++d)
+            for (int pw = 0; pw < 6; ++pw) m1[d][pw] = S[d * 6 + pw];
+        const double *pq = dc.fprim0 + (size_t)f * M;
+        const double lam0 = pq[D + 1];
+        sep_moments<D>(m1, pref_of(pq[0], lam0, D), dc.nxi / (2.0 * lam0),
+                       dc.nxi * (dc.nxi + 2.0) / (4.0 * lam0 * lam0), Ssep);
+        S = Ssep;
+    }
     double Mc[M * M], Tc[D][M * M];
     {
         int t = 0;
@@ -717,13 +820,11 @@ __global__ void __launch_bounds__(256) k_wall_sum(DevCase<T> dc)
 //          to f_nxt, and the moments sum_k w psi_k R_k of the flux residual for
 //          the W update (Eq. macroscopicUpdata / macroscopicFlux).
 template <typename T, int D, int NC, int TV>
-__global__ void __launch_bounds__(256) k_gather(DevCase<T> dc)
+__device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, const int vt, T *sg)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sg = reinterpret_cast<T *>(smem_raw);
     constexpr int V = 32 * TV;
     constexpr int M = D + 2;
-    const int p = blockIdx.x, vt = blockIdx.y, k0 = vt * V;
+    const int k0 = vt * V;
     const int cb = p * dc.P;
     const int npc = min(dc.P, dc.C - cb);
     const int rb = dc.ring_ptr[p], re = dc.ring_ptr[p + 1];
@@ -890,6 +991,28 @@ __global__ void __launch_bounds__(256) k_gather(DevCase<T> dc)
     }
 }
 
+template <typename T, int D, int NC, int TV>
+__global__ void __launch_bounds__(256) k_gather(DevCase<T> dc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    gather_item<T, D, NC, TV>(dc, blockIdx.x, blockIdx.y, reinterpret_cast<T *>(smem_raw));
+}
+
+// Persistent gather over many cases: a fixed grid of CTAs walks a work list of
+// (case, patch, velocity tile) items; each item is exactly the CTA of k_gather
+// for that case, so every case gets bit-identical results alone or batched.
+template <typename T, int D, int NC, int TV>
+__global__ void __launch_bounds__(256) k_gather_batch(const DevCase<T> *__restrict__ cases, const int4 *__restrict__ work,
+                                                      int nwork)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int4 it = work[w];
+        gather_item<T, D, NC, TV>(cases[it.x], it.y, it.z, reinterpret_cast<T *>(smem_raw));
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------ W update
 template <typename T, int D, int NC>
 __global__ void __launch_bounds__(256) k_update_W(DevCase<T> dc)
@@ -962,7 +1085,7 @@ __global__ void k_residual(const double *res_part, int nblocks, double *res)
 // ------------------------------------------------------------ stage 2
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
-template <> struct Vec4<double> { using type = double4; };
+template <> struct Vec4<double> { using type = double4_32a; };
 
 // 4 consecutive velocities per lane (rows are padded to a multiple of 32, so
 // every row start is 16-byte aligned for FP32 and 32-byte aligned for FP64)
@@ -1111,10 +1234,9 @@ static cudaError_t gather_launch(const DevCase<T> &dc, size_t smem, cudaStream_t
 }
 
 template <typename T, int D, int NC>
-static cudaError_t step_dn(const DevCase<T> &dc, const StepConfig &cfg, cudaStream_t st, cudaEvent_t *ev)
+static void pre_gather(const DevCase<T> &dc, cudaStream_t st, cudaEvent_t *ev)
 {
     const int C = dc.C, F = dc.F;
-    // ev (optional): N_GROUPS + 1 events bracketing the kernel groups
     auto mark = [&](int i) {
         if (ev) cudaEventRecord(ev[i], st);
     };
@@ -1126,12 +1248,32 @@ static cudaError_t step_dn(const DevCase<T> &dc, const StepConfig &cfg, cudaStre
         k_face_pre<T, D, NC><<<cdiv(F, 128), 128, 0, st>>>(dc);
         k_face_sum1<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
         k_face_fin1<T, D, NC><<<cdiv(F, 128), 128, 0, st>>>(dc);
-        k_face_sum2<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
+        if (dc.sep) k_face_sum2_sep<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
+        else k_face_sum2<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
         k_face_fin2<T, D, NC><<<cdiv(F, 64), 64, 0, st>>>(dc);
     }
     mark(2);
     if (dc.NW > 0) k_wall_sum<T, D, NC><<<dc.NW, 256, 0, st>>>(dc);
     mark(3);
+}
+
+template <typename T, int D, int NC>
+static void post_gather(const DevCase<T> &dc, const StepConfig &cfg, cudaStream_t st, cudaEvent_t *ev)
+{
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord(ev[i], st);
+    };
+    mark(4);
+    k_update_W<T, D, NC><<<cfg.n_res_blocks, 256, 0, st>>>(dc);
+    mark(5);
+    k_collide<T, D, NC><<<cdiv(dc.C, 8), 256, 0, st>>>(dc);
+    mark(6);
+}
+
+template <typename T, int D, int NC>
+static cudaError_t step_dn(const DevCase<T> &dc, const StepConfig &cfg, cudaStream_t st, cudaEvent_t *ev)
+{
+    pre_gather<T, D, NC>(dc, st, ev);
     cudaError_t e;
     switch (dc.vtile / 32) {
     case 1: e = gather_launch<T, D, NC, 1>(dc, cfg.smem, st); break;
@@ -1140,12 +1282,86 @@ static cudaError_t step_dn(const DevCase<T> &dc, const StepConfig &cfg, cudaStre
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    mark(4);
-    k_update_W<T, D, NC><<<cfg.n_res_blocks, 256, 0, st>>>(dc);
-    mark(5);
-    k_collide<T, D, NC><<<cdiv(C, 8), 256, 0, st>>>(dc);
-    mark(6);
+    post_gather<T, D, NC>(dc, cfg, st, ev);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pre_gather(const DevCase<T> &dc, cudaStream_t st)
+{
+    if (dc.D == 2) pre_gather<T, 2, 2>(dc, st, nullptr);
+    else pre_gather<T, 3, 1>(dc, st, nullptr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_post_gather(const DevCase<T> &dc, const StepConfig &cfg, cudaStream_t st)
+{
+    if (dc.D == 2) post_gather<T, 2, 2>(dc, cfg, st, nullptr);
+    else post_gather<T, 3, 1>(dc, cfg, st, nullptr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather(const DevCase<T> &dc, size_t smem, cudaStream_t st)
+{
+    const int tv = dc.vtile / 32;
+    if (dc.D == 2) {
+        if (tv == 1) return gather_launch<T, 2, 2, 1>(dc, smem, st);
+        if (tv == 2) return gather_launch<T, 2, 2, 2>(dc, smem, st);
+        if (tv == 4) return gather_launch<T, 2, 2, 4>(dc, smem, st);
+    } else {
+        if (tv == 1) return gather_launch<T, 3, 1, 1>(dc, smem, st);
+        if (tv == 2) return gather_launch<T, 3, 1, 2>(dc, smem, st);
+        if (tv == 4) return gather_launch<T, 3, 1, 4>(dc, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int D, int NC, int TV>
+static cudaError_t gather_batch_launch(const DevCase<T> *cases, const int4 *work, int nwork, int grid, size_t smem,
+                                       cudaStream_t st)
+{
+    auto kern = k_gather_batch<T, D, NC, TV>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, smem, st>>>(cases, work, nwork);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather_batch(int D, int vtile, const DevCase<T> *cases, const int4 *work, int nwork, int grid,
+                                size_t smem, cudaStream_t st)
+{
+    const int tv = vtile / 32;
+    if (D == 2) {
+        if (tv == 1) return gather_batch_launch<T, 2, 2, 1>(cases, work, nwork, grid, smem, st);
+        if (tv == 2) return gather_batch_launch<T, 2, 2, 2>(cases, work, nwork, grid, smem, st);
+        if (tv == 4) return gather_batch_launch<T, 2, 2, 4>(cases, work, nwork, grid, smem, st);
+    } else {
+        if (tv == 1) return gather_batch_launch<T, 3, 1, 1>(cases, work, nwork, grid, smem, st);
+        if (tv == 2) return gather_batch_launch<T, 3, 1, 2>(cases, work, nwork, grid, smem, st);
+        if (tv == 4) return gather_batch_launch<T, 3, 1, 4>(cases, work, nwork, grid, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// CTAs of the gather kernel that fit on the device at once (persistent grid)
+template <typename T>
+int gather_resident_ctas(int D, int vtile, size_t smem)
+{
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int tv = vtile / 32;
+    const void *fn = nullptr;
+    if (D == 2) fn = tv == 1 ? (const void *)k_gather_batch<T, 2, 2, 1> : tv == 2 ? (const void *)k_gather_batch<T, 2, 2, 2>
+                                                                               : (const void *)k_gather_batch<T, 2, 2, 4>;
+    else fn = tv == 1 ? (const void *)k_gather_batch<T, 3, 1, 1> : tv == 2 ? (const void *)k_gather_batch<T, 3, 1, 2>
+                                                                      : (const void *)k_gather_batch<T, 3, 1, 4>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, smem);
+    return std::max(1, per) * std::max(1, nsm);
 }
 
 template <typename T>
@@ -1229,6 +1445,16 @@ cudaError_t launch_check(const double *W, int C, int M, int *flags, cudaStream_t
     return cudaGetLastError();
 }
 
+template cudaError_t launch_pre_gather<double>(const DevCase<double> &, cudaStream_t);
+template cudaError_t launch_pre_gather<float>(const DevCase<float> &, cudaStream_t);
+template cudaError_t launch_post_gather<double>(const DevCase<double> &, const StepConfig &, cudaStream_t);
+template cudaError_t launch_post_gather<float>(const DevCase<float> &, const StepConfig &, cudaStream_t);
+template cudaError_t launch_gather<double>(const DevCase<double> &, size_t, cudaStream_t);
+template cudaError_t launch_gather<float>(const DevCase<float> &, size_t, cudaStream_t);
+template cudaError_t launch_gather_batch<double>(int, int, const DevCase<double> *, const int4 *, int, int, size_t, cudaStream_t);
+template cudaError_t launch_gather_batch<float>(int, int, const DevCase<float> *, const int4 *, int, int, size_t, cudaStream_t);
+template int gather_resident_ctas<double>(int, int, size_t);
+template int gather_resident_ctas<float>(int, int, size_t);
 template cudaError_t launch_step<double>(const DevCase<double> &, const StepConfig &, cudaStream_t, cudaEvent_t *);
 template cudaError_t launch_step<float>(const DevCase<float> &, const StepConfig &, cudaStream_t, cudaEvent_t *);
 template cudaError_t launch_init<double>(const DevCase<double> &, cudaStream_t);

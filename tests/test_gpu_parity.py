@@ -215,3 +215,25 @@ def test_full_size_mach5_fp32_stays_physical():
         g.check()
     rho, U, T, q = g.moments()
     assert rho.min() > 0 and T.min() > 0 and np.isfinite(q).all()
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_unstructured_velocity_set(D):
+    """A non-tensor discrete velocity set (jittered points, arbitrary positive
+    weights, shuffled order) takes the general per-velocity face sums."""
+    rng = np.random.default_rng(21)
+    if D == 2:
+        vg = cs.cartesian_vgrid((17, 15), (-6, -5), (6, 5))
+        case = cs.cylinder_case(n_cells=900, nvx=4, nvy=4, mach=2.0)
+    else:
+        vg = cs.cartesian_vgrid((9, 8, 8), (-5, -5, -5), (5, 5, 5))
+        case = cs.sphere_case(n_cells=1500, nv=4, vmax=5.0, mach=1.5)
+    perm = rng.permutation(len(vg["w"]))
+    u = vg["u"][perm] + rng.uniform(-0.15, 0.15, size=vg["u"].shape)
+    w = vg["w"][perm] * rng.uniform(0.8, 1.2, size=len(perm))
+    vgu = {"dim": D, "u": u, "w": w, "cart_n": [0, 0, 0]}
+    case = dict(case, vgrid=vgu)
+    o, g = _pair(case, perturb=0.05)
+    o.step(2)
+    g.step(2)
+    _compare(o, g, what=f"unstructured DVS {D}D")
