@@ -154,6 +154,42 @@ def _cpu_baseline(case, steps=1):
             "sample": f"{steps} full step(s) of the same case on the host cores (OpenMP), {dt:.1f} s"}
 
 
+def _serving(args, torch, lib):
+    """Serving leg: closed run (all requests at t = 0) to calibrate capacity,
+    then Poisson arrivals at 1.5x that capacity; p50 / p99 of the time from
+    arrival to completion and the aggregate cell-velocity rate."""
+    import numpy as np
+    from paper_2412_06546_gb300 import serving
+    reqs = serving.request_stream(args.serve_n, seed=4)
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def run(arrivals):
+        srv = lib.Server(budget, args.serve_slots, args.serve_tick)
+        t0 = srv.stats()["clock"]
+        tickets = [srv.submit(c, args.serve_tol, args.serve_max_steps, t_arrive=t0 + a) for c, a in zip(reqs, arrivals)]
+        ok = srv.run(args.serve_timeout)
+        st = srv.stats()
+        res = [srv.poll(t) for t in tickets]
+        srv.close()
+        lat = np.array([r["t_done"] - r["t_arrive"] for r in res])
+        span = max(r["t_done"] for r in res) - t0
+        conv = sum(1 for r in res if r["state"] == lib.REQ_DONE and r["status"] == 0)
+        return ok, lat, span, st["total_cvu"], conv, res
+
+    ok0, lat0, span0, cvu0, conv0, _ = run(np.zeros(len(reqs)))
+    rate = 1.5 * len(reqs) / span0                 # offered load 1.5x the closed-run capacity
+    arr = serving.poisson_arrivals(len(reqs), rate, seed=44)
+    ok1, lat1, span1, cvu1, conv1, res1 = run(arr)
+    return {"requests": len(reqs), "tol": args.serve_tol, "max_steps": args.serve_max_steps,
+            "steps_per_tick": args.serve_tick, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
+            "arrival_rate_per_s": rate, "p50_s": float(np.percentile(lat1, 50)), "p99_s": float(np.percentile(lat1, 99)),
+            "aggregate_cvu_per_s": cvu1 / span1, "converged": conv1, "finished": bool(ok1),
+            "closed_run": {"makespan_s": span0, "aggregate_cvu_per_s": cvu0 / span0, "p50_s": float(np.percentile(lat0, 50)),
+                           "p99_s": float(np.percentile(lat0, 99)), "converged": conv0},
+            "workload": "seeded cavity/cylinder stream: cells 1k-4k, N^2 velocities N in [16, 32], "
+                        "Kn log-uniform [1e-3, 10], Mach [0.1, 6], FP32 storage"}
+
+
 def run_reference(args):
     dist_rank = int(os.environ.get("RANK", "0"))
     if dist_rank != 0:
@@ -194,6 +230,14 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=0)
     ap.add_argument("--ref-warmup", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-n", type=int, default=24)
+    ap.add_argument("--serve-tol", type=float, default=1e-4)
+    ap.add_argument("--serve-max-steps", type=int, default=6000)
+    ap.add_argument("--serve-tick", type=int, default=25)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-budget-gb", type=float, default=8.0)
+    ap.add_argument("--serve-timeout", type=float, default=240.0)
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--patch", type=int, default=0)
     ap.add_argument("--vtile", type=int, default=0)
     args = ap.parse_args()
@@ -267,6 +311,10 @@ def main():
     v64 = ws * C * Nv / (ms64 * 1e-3)
     g64.close()
 
+    serving_res = None
+    if not args.no_serving:
+        serving_res = _serving(args, torch, _lib)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(case)
@@ -288,6 +336,8 @@ def main():
         "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
         "step_hbm_frac_1R1W": value / ws * 4 * nc * 2 / (peak * 1e9),
     }
+    if serving_res:
+        line["serving"] = serving_res
     if cpu:
         line["cpu_baseline"] = cpu
     if rank == 0:

@@ -182,6 +182,57 @@ ugks_status ugks_batch_create(ugks_case *const *cases, int32_t n, void *stream, 
 ugks_status ugks_batch_step(ugks_batch *b, int32_t nsteps);
 void ugks_batch_destroy(ugks_batch *b);
 
+/* ---- Serving loop (continuous batching of independent cases) ----
+ * Requests arrive (at a time on the server clock); every ugks_server_tick
+ * admits arrived requests, first fit in arrival order, while a slot is free
+ * and the request's estimated device footprint (two copies of f plus the
+ * O(cells + faces) arrays) fits the remaining budget; steps every running case
+ * steps_per_tick times in batches (ugks_batch: one persistent gather launch per
+ * step, CUDA-graph replay); then reads each running case's residual and retires
+ * the converged ones (max_m r_m < tol), those at max_steps (status
+ * UGKS_ENOTCONVERGED) and those with a numeric failure, keeping their rho, U,
+ * T, q on the host and freeing their device memory.  The server is
+ * thread-safe (one mutex); its inputs are copied at submission. */
+enum { UGKS_REQ_QUEUED = 0, UGKS_REQ_RUNNING = 1, UGKS_REQ_DONE = 2, UGKS_REQ_FAILED = 3 };
+
+typedef struct {
+    int32_t state;            /* UGKS_REQ_* */
+    int32_t status;           /* UGKS_OK, UGKS_ENOTCONVERGED, or the failing call's status */
+    int64_t steps;            /* steps taken */
+    double residual[5];       /* residual of the last step (dim+2 used) */
+    double t_arrive, t_admit, t_done;   /* server clock, seconds; -1 if not yet */
+    size_t footprint_bytes;   /* admission estimate */
+    size_t device_bytes;      /* bytes the case actually held */
+    int64_t n_cells, nv;
+} ugks_result;
+
+typedef struct {
+    size_t device_budget, device_used;
+    int32_t n_running, n_queued;
+    int64_t total_cvu;        /* cell-velocity updates executed so far */
+    double clock;             /* server clock now, seconds */
+} ugks_server_stats_t;
+
+typedef struct ugks_server ugks_server;
+
+/* device_budget_bytes: device memory the admitted cases may hold in total;
+ * max_slots: cases running at once; steps_per_tick: batched steps between
+ * residual checks; stream: cudaStream_t (NULL: the server's own). */
+ugks_status ugks_server_create(size_t device_budget_bytes, int32_t max_slots, int32_t steps_per_tick, void *stream,
+                               ugks_server **out);
+/* Queue a case (inputs copied).  t_arrive >= 0: arrival time on the server
+ * clock (the request is not admitted before it); < 0: now.  Returns a ticket. */
+ugks_status ugks_server_submit(ugks_server *s, const ugks_mesh *mesh, const ugks_vgrid *vgrid,
+                               const ugks_params *params, double tol, int64_t max_steps, double t_arrive,
+                               uint64_t *ticket);
+/* One round: admit, step, retire.  Reports the running and queued counts. */
+ugks_status ugks_server_tick(ugks_server *s, int32_t *n_running, int32_t *n_queued);
+ugks_status ugks_server_poll(ugks_server *s, uint64_t ticket, ugks_result *out);
+/* rho[C], U[C][dim], T[C], q[C][dim] of a finished request (caller order). */
+ugks_status ugks_server_moments(ugks_server *s, uint64_t ticket, double *rho, double *U, double *T, double *q);
+ugks_status ugks_server_stats(ugks_server *s, ugks_server_stats_t *out);
+void ugks_server_destroy(ugks_server *s);
+
 /* Sizes and tiling of a case. */
 ugks_status ugks_info(const ugks_case *c, ugks_info_t *info);
 

@@ -69,6 +69,20 @@ class Info(ct.Structure):
                 ("kernel_launches_per_step", ct.c_int64)]
 
 
+class Result(ct.Structure):
+    _fields_ = [("state", ct.c_int32), ("status", ct.c_int32), ("steps", ct.c_int64),
+                ("residual", ct.c_double * 5), ("t_arrive", ct.c_double), ("t_admit", ct.c_double),
+                ("t_done", ct.c_double), ("footprint_bytes", ct.c_size_t), ("device_bytes", ct.c_size_t),
+                ("n_cells", ct.c_int64), ("nv", ct.c_int64)]
+
+
+class ServerStats(ct.Structure):
+    _fields_ = [("device_budget", ct.c_size_t), ("device_used", ct.c_size_t), ("n_running", ct.c_int32),
+                ("n_queued", ct.c_int32), ("total_cvu", ct.c_int64), ("clock", ct.c_double)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
 EXPORTS = {
     "ugks_create": (ct.c_int, [ct.POINTER(Mesh), ct.POINTER(VGrid), ct.POINTER(Params), ct.POINTER(Alloc),
                                ct.c_void_p, ct.POINTER(ct.c_void_p)]),
@@ -86,6 +100,14 @@ EXPORTS = {
     "ugks_batch_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int32, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
     "ugks_batch_step": (ct.c_int, [ct.c_void_p, ct.c_int32]),
     "ugks_batch_destroy": (None, [ct.c_void_p]),
+    "ugks_server_create": (ct.c_int, [ct.c_size_t, ct.c_int32, ct.c_int32, ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    "ugks_server_submit": (ct.c_int, [ct.c_void_p, ct.POINTER(Mesh), ct.POINTER(VGrid), ct.POINTER(Params),
+                                      ct.c_double, ct.c_int64, ct.c_double, ct.POINTER(ct.c_uint64)]),
+    "ugks_server_tick": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32)]),
+    "ugks_server_poll": (ct.c_int, [ct.c_void_p, ct.c_uint64, ct.POINTER(Result)]),
+    "ugks_server_moments": (ct.c_int, [ct.c_void_p, ct.c_uint64, D_P, D_P, D_P, D_P]),
+    "ugks_server_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(ServerStats)]),
+    "ugks_server_destroy": (None, [ct.c_void_p]),
     "ugks_destroy": (None, [ct.c_void_p]),
     "ugks_last_error": (ct.c_char_p, []),
 }
@@ -282,6 +304,73 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             load().ugks_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+class Server:
+    """Continuous-batching serving loop (``ugks_server_*``): submit cases with
+    arrival times, call ``tick`` until everything is done, poll the results."""
+
+    def __init__(self, budget_bytes, max_slots, steps_per_tick, stream=None):
+        L = load()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = ct.c_void_p()
+        check(L.ugks_server_create(int(budget_bytes), int(max_slots), int(steps_per_tick), ct.c_void_p(stream or 0),
+                                   ct.byref(h)))
+        self._h = h
+        self.shapes = {}
+
+    def submit(self, case, tol, max_steps, t_arrive=-1.0, precision=FP32, init=None):
+        (m, v, p), keep = make_structs(case["mesh"], case["vgrid"], case["params"],
+                                       case.get("init") if init is None else init, precision)
+        t = ct.c_uint64()
+        check(load().ugks_server_submit(self._h, ct.byref(m), ct.byref(v), ct.byref(p), float(tol), int(max_steps),
+                                        float(t_arrive), ct.byref(t)))
+        self.shapes[t.value] = (len(case["mesh"]["cell_vol"]), int(case["mesh"]["dim"]))
+        return t.value
+
+    def tick(self):
+        r, q = ct.c_int32(), ct.c_int32()
+        check(load().ugks_server_tick(self._h, ct.byref(r), ct.byref(q)))
+        return r.value, q.value
+
+    def poll(self, ticket):
+        res = Result()
+        check(load().ugks_server_poll(self._h, int(ticket), ct.byref(res)))
+        out = {k: getattr(res, k) for k, _ in Result._fields_}
+        out["residual"] = list(res.residual)
+        return out
+
+    def moments(self, ticket):
+        C, D = self.shapes[ticket]
+        rho, U, T, q = np.empty(C), np.empty((C, D)), np.empty(C), np.empty((C, D))
+        check(load().ugks_server_moments(self._h, int(ticket), _p(rho), _p(U), _p(T), _p(q)))
+        return rho, U, T, q
+
+    def stats(self):
+        st = ServerStats()
+        check(load().ugks_server_stats(self._h, ct.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def run(self, timeout_s=600.0, idle_sleep=0.0005):
+        """Tick until no request is running or queued (or the timeout)."""
+        import time
+        t0 = time.time()
+        while time.time() - t0 < timeout_s:
+            running, queued = self.tick()
+            if running == 0 and queued == 0:
+                return True
+            if running == 0:
+                time.sleep(idle_sleep)
+        return False
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ugks_server_destroy(self._h)
             self._h = None
 
     __del__ = close

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libugks.so")
-SOURCES = ["ugks_kernels.cu", "ugks_host.cu", "ugks_noalloc.cu"]
+SOURCES = ["ugks_kernels.cu", "ugks_host.cu", "ugks_noalloc.cu", "ugks_server.cu"]
 HEADERS = ["ugks_device.cuh", "ugks_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
