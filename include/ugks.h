@@ -169,9 +169,10 @@ ugks_status ugks_profile_begin(ugks_case *c, int32_t max_steps);
 ugks_status ugks_profile_end(ugks_case *c, double *ms, int32_t n, int32_t *steps);
 
 /* Batched stepping of several cases (one GPU).  The cases must share the
- * dimension, precision and velocity tile.  Each batch step runs every case's
- * gather pass in one persistent kernel that walks a (case, patch, velocity
- * tile) work list, and the other kernels of every case on parallel graph
+ * dimension and precision.  Each batch step runs every case's gather pass in
+ * one persistent kernel per velocity-tile width present in the batch, which
+ * walks a (case, patch, velocity tile) work list, and the other kernels of
+ * every case on parallel graph
  * branches; the whole step is captured once as a CUDA graph on `stream`
  * (cudaStream_t, NULL: a stream of the batch's own) and replayed.  Results
  * are bit-identical to stepping each case alone with ugks_step.  The cases

@@ -40,6 +40,15 @@ template <int D> struct Poly {
 
 enum { FT_INTERIOR = 0, FT_WALL = 1, FT_FARFIELD = 2, FT_PERIODIC = 3 };
 
+// layout of the values of one gather entry (cell c, face f): a = LSQ
+// coefficient of the neighbour across f (0 for a wall), rs = x_f - x_c,
+// n = unit normal of f pointing out of c, ro = x_f - x_other (periodic image;
+// 0 for far-field ghosts), cs = -S_f / |Omega_c|
+template <int D> struct GEnt {
+    static constexpr int A = 0, RS = D, N = 2 * D, RO = 3 * D, CS = 4 * D;
+    static constexpr int LEN = (4 * D + 1 + 3) / 4 * 4;
+};
+
 // Everything a kernel needs, by value.  Geometry used inside velocity loops is
 // held in the arithmetic type T; macroscopic data is FP64.
 template <typename T>
@@ -67,7 +76,13 @@ struct DevCase {
     const double *cf_r_d;
     const T *cf_r;                // x_f - x_c (periodic image on the neighbour side)
     const T *cf_coef;             // -sigma S_f / |Omega_c|
-    const short *cf_sL, *cf_sR;   // local slope slot of the owner / neighbour in the patch
+    // gather entries, one per (cell, face) in cf order, in the cell's own
+    // orientation: gi = {other, face, type, patch slot of other}, where other
+    // is the neighbour cell (interior, periodic), the ghost slot (far field) or
+    // the wall slot (wall); gf = GEnt<D> values (LSQ coefficient, offsets,
+    // outward normal, -S_f/|Omega_c|)
+    const int4 *gi;
+    const T *gf;
     const double *eps2_d;
     const T *eps2;
     // faces
@@ -218,6 +233,84 @@ __device__ __forceinline__ void shakhov_fplus(const T *rec, const T u[3], T fp[N
     if (NC == 2) fp[NC - 1] = H * rec[CR_NB] * (T(1) + kqc * (l2c2 - T(D)));
 }
 
+// TV consecutive values at a TV*sizeof(T)-aligned address, moved in chunks
+// of at most 16 bytes (read-only data through the non-coherent path)
+template <typename T, int N> struct VecOf;
+template <> struct VecOf<float, 1> { using type = float; };
+template <> struct VecOf<float, 2> { using type = float2; };
+template <> struct VecOf<float, 4> { using type = float4; };
+template <> struct VecOf<double, 1> { using type = double; };
+template <> struct VecOf<double, 2> { using type = double2; };
+template <typename T, int TV> constexpr int vec_chunk() { return TV * (int)sizeof(T) <= 16 ? TV : 16 / (int)sizeof(T); }
+
+template <typename T, int TV>
+__device__ __forceinline__ void ldv(const T *__restrict__ p, T (&x)[TV])
+{
+    constexpr int CH = vec_chunk<T, TV>();
+    using V = typename VecOf<T, CH>::type;
+#pragma unroll
+    for (int i = 0; i < TV / CH; ++i) {
+        const V v = __ldg(reinterpret_cast<const V *>(p) + i);
+        const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) x[i * CH + j] = e[j];
+    }
+}
+// the same from and to shared memory
+template <typename T, int TV>
+__device__ __forceinline__ void ldv_s(const T *p, T (&x)[TV])
+{
+    constexpr int CH = vec_chunk<T, TV>();
+    using V = typename VecOf<T, CH>::type;
+#pragma unroll
+    for (int i = 0; i < TV / CH; ++i) {
+        const V v = reinterpret_cast<const V *>(p)[i];
+        const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) x[i * CH + j] = e[j];
+    }
+}
+template <typename T, int TV>
+__device__ __forceinline__ void stv(T *p, const T (&x)[TV])
+{
+    constexpr int CH = vec_chunk<T, TV>();
+    using V = typename VecOf<T, CH>::type;
+#pragma unroll
+    for (int i = 0; i < TV / CH; ++i) {
+        V v;
+        T *e = reinterpret_cast<T *>(&v);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) e[j] = x[i * CH + j];
+        reinterpret_cast<V *>(p)[i] = v;
+    }
+}
+
+// copy a 16-byte aligned record of N values into registers with vector loads
+template <int N>
+__device__ __forceinline__ void load_rec(const float *__restrict__ p, float (&r)[N])
+{
+    static_assert(N % 4 == 0, "record length");
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + i);
+        r[4 * i] = v.x;
+        r[4 * i + 1] = v.y;
+        r[4 * i + 2] = v.z;
+        r[4 * i + 3] = v.w;
+    }
+}
+template <int N>
+__device__ __forceinline__ void load_rec(const double *__restrict__ p, double (&r)[N])
+{
+    static_assert(N % 2 == 0, "record length");
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + i);
+        r[2 * i] = v.x;
+        r[2 * i + 1] = v.y;
+    }
+}
+
 // Micro reconstruction of cell c at velocity index k (Sec. 3.1 Step 2):
 // least-squares slope grad = sum_j a_cj (f_j - f_c), Venkatakrishnan factor
 // phi = min over the faces of c of (D1^2 + eps^2 + 2 D1 D2) / (D1^2 + 2 D2^2 +
@@ -306,6 +399,113 @@ __device__ __forceinline__ void cell_slope(const DevCase<T> &dc, const T *__rest
     }
 }
 
+// cell_slope for the TV consecutive velocities of this lane: the same
+// arithmetic per velocity, with every face entry read once for all of them.
+// fl points at f_cur + the lane's first velocity; fi returns f_c.  The face
+// loops are unrolled so that the entry and neighbour loads of several faces
+// are in flight together (the pass is bound by their latency).
+template <typename T, int D, int NC, int TV>
+__device__ __forceinline__ void cell_slope_tv(const DevCase<T> &dc, const T *__restrict__ fl, int c,
+                                              const T (&u)[3][TV], T (&g)[NC][D][TV], T (&fi)[NC][TV])
+{
+    using E = GEnt<D>;
+    constexpr int HA = (2 * D + 3) / 4 * 4;       // a and rs, rounded to whole vector loads
+    const int nvp = dc.nvp;
+    const size_t rs = (size_t)NC * nvp;
+    T vmax[NC][TV], vmin[NC][TV];
+    const T *fc = fl + (size_t)c * rs;
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+        ldv<T, TV>(fc + (size_t)m * nvp, fi[m]);
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+            vmax[m][j] = vmin[m][j] = fi[m][j];
+#pragma unroll
+            for (int d = 0; d < D; ++d) g[m][d][j] = 0;
+        }
+    }
+    const int e0 = __ldg(dc.cf_ptr + c), e1 = __ldg(dc.cf_ptr + c + 1);
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+        const int4 gi = __ldg(dc.gi + e);
+        if (gi.z == FT_WALL) continue;
+        T ge[HA];
+        load_rec<HA>(dc.gf + (size_t)e * E::LEN, ge);
+        T fj[NC][TV];
+        if (gi.z == FT_FARFIELD) {
+            T gr[GREC];
+            load_rec<GREC>(dc.grec + (size_t)gi.x * GREC, gr);
+#pragma unroll
+            for (int j = 0; j < TV; ++j) {
+                const T uj[3] = {u[0][j], u[1][j], u[2][j]};
+                const T H = maxwell_h<T, D>(gr, uj);
+                fj[0][j] = H;
+                if (NC == 2) fj[NC - 1][j] = gr[GR_NB] * H;
+            }
+        } else {
+            const T *fo = fl + (size_t)gi.x * rs;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) ldv<T, TV>(fo + (size_t)m * nvp, fj[m]);
+        }
+#pragma unroll
+        for (int m = 0; m < NC; ++m)
+#pragma unroll
+            for (int j = 0; j < TV; ++j) {
+                const T df = fj[m][j] - fi[m][j];
+#pragma unroll
+                for (int d = 0; d < D; ++d) g[m][d][j] += ge[E::A + d] * df;
+                vmax[m][j] = fj[m][j] > vmax[m][j] ? fj[m][j] : vmax[m][j];
+                vmin[m][j] = fj[m][j] < vmin[m][j] ? fj[m][j] : vmin[m][j];
+            }
+    }
+    const T e2 = __ldg(dc.eps2 + c);
+    T phi[NC][TV], dmin[NC][TV];
+#pragma unroll
+    for (int m = 0; m < NC; ++m)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+            phi[m][j] = T(1);
+            dmin[m][j] = T(0);
+        }
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) {
+        T ge[HA];
+        load_rec<HA>(dc.gf + (size_t)e * E::LEN, ge);
+#pragma unroll
+        for (int m = 0; m < NC; ++m)
+#pragma unroll
+            for (int j = 0; j < TV; ++j) {
+                T d2 = 0;
+#pragma unroll
+                for (int d = 0; d < D; ++d) d2 += g[m][d][j] * ge[E::RS + d];
+                dmin[m][j] = d2 < dmin[m][j] ? d2 : dmin[m][j];
+                if (dc.limiter) {
+                    const T d1 = d2 > T(0) ? vmax[m][j] - fi[m][j] : vmin[m][j] - fi[m][j];
+                    const T a2 = d1 * d1 + e2;
+                    const T num = a2 + T(2) * d1 * d2;
+                    const T den = a2 + d2 * (T(2) * d2 + d1);
+                    const T ph = den > T(0) ? fdiv(num, den) : T(1);
+                    phi[m][j] = ph < phi[m][j] ? ph : phi[m][j];
+                }
+            }
+    }
+    const T dt = dc.dtT;
+#pragma unroll
+    for (int m = 0; m < NC; ++m)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+            T ug = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) ug += u[d][j] * g[m][d][j];
+            const T foot = -dt * ug;
+            const T v = fi[m][j] + phi[m][j] * (dmin[m][j] + (foot < T(0) ? foot : T(0)));
+            T sc = phi[m][j];
+            if (v < T(0)) sc *= fi[m][j] > T(0) ? fdiv(fi[m][j], fi[m][j] - v) : T(0);
+#pragma unroll
+            for (int d = 0; d < D; ++d) g[m][d][j] *= sc;
+        }
+}
+
 // Interface flux of Eq. microscopicFlux with the distribution of Eq.
 // fullSolution integrated over the step (q1..q5):
 // F = u_n [q1 f_up + q2 u.grad f_up + H0(c) P(c)], the equilibrium part
@@ -331,32 +531,6 @@ __device__ __forceinline__ T poly_eval(const T *__restrict__ a, const T c[D], T 
 #pragma unroll
     for (int e = 0; e < D; ++e) g += a[t + NB + e] * c[e];
     return p + g * c2;
-}
-
-// copy a 16-byte aligned record of N values into registers with vector loads
-template <int N>
-__device__ __forceinline__ void load_rec(const float *__restrict__ p, float (&r)[N])
-{
-    static_assert(N % 4 == 0, "record length");
-#pragma unroll
-    for (int i = 0; i < N / 4; ++i) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + i);
-        r[4 * i] = v.x;
-        r[4 * i + 1] = v.y;
-        r[4 * i + 2] = v.z;
-        r[4 * i + 3] = v.w;
-    }
-}
-template <int N>
-__device__ __forceinline__ void load_rec(const double *__restrict__ p, double (&r)[N])
-{
-    static_assert(N % 2 == 0, "record length");
-#pragma unroll
-    for (int i = 0; i < N / 2; ++i) {
-        const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + i);
-        r[2 * i] = v.x;
-        r[2 * i + 1] = v.y;
-    }
 }
 
 template <typename T, int D, int NC>

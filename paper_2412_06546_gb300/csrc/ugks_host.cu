@@ -141,7 +141,8 @@ struct Host {
     std::vector<int> cf_ptr, cf_face;
     std::vector<signed char> cf_side;
     std::vector<double> cf_r, cf_coef;
-    std::vector<short> cf_sL, cf_sR;
+    std::vector<double> gf;          // gather entry values [ncf][GEnt<D>::LEN]
+    std::vector<int> gi;             // gather entry ids [ncf][4] (patch slots: build_patches)
     std::vector<int> nb_ptr, nb_id;
     std::vector<double> nb_a, eps2, vol;
     std::vector<int> fL, fR, faux, ftag, gface, wface;
@@ -391,6 +392,31 @@ void preprocess(const ugks_mesh *m, const ugks_params *p, int P, Host &h)
         h.eps2[c] = Kh * Kh * Kh;
     }
 
+    // ---- gather entry values of every (cell, face), in the cell's own
+    //      orientation: LSQ coefficient, x_f - x_c, outward normal,
+    //      x_f - x_other, -S_f / |Omega_c|
+    const int GL = D == 2 ? ugks::GEnt<2>::LEN : ugks::GEnt<3>::LEN;
+    h.gf.assign((size_t)ncf * GL, 0.0);
+    for (int c = 0; c < C; ++c) {
+        int q = h.nb_ptr[c];
+        for (int e = h.cf_ptr[c]; e < h.cf_ptr[c + 1]; ++e) {
+            const int f = h.cf_face[e], t = h.ftype[f];
+            const bool own = h.cf_side[e] == 0;
+            double *g = &h.gf[(size_t)e * GL];
+            if (t != UGKS_FACE_WALL) {
+                for (int d = 0; d < D; ++d) g[d] = h.nb_a[(size_t)q * D + d];
+                ++q;
+            }
+            for (int d = 0; d < D; ++d) {
+                g[D + d] = h.cf_r[(size_t)e * D + d];
+                g[2 * D + d] = own ? h.fn[(size_t)f * D + d] : -h.fn[(size_t)f * D + d];
+                if (t == UGKS_FACE_INTERIOR || t == UGKS_FACE_PERIODIC)
+                    g[3 * D + d] = own ? h.frR[(size_t)f * D + d] : h.frL[(size_t)f * D + d];
+            }
+            g[4 * D] = -m->face_S[f] / h.vol[c];
+        }
+    }
+
     build_patches(h, C, P);
 }
 
@@ -404,8 +430,7 @@ void build_patches(Host &h, int C, int P)
     h.max_slope = 0;
     const int np = (C + P - 1) / P;
     h.ring_ptr.assign(np + 1, 0);
-    h.cf_sL.assign(ncf, -1);
-    h.cf_sR.assign(ncf, -1);
+    h.gi.assign((size_t)ncf * 4, -1);
     std::vector<int> slot_of(C, -1);
     for (int pi = 0; pi < np; ++pi) {
         const int cb = pi * P, ce = std::min(C, cb + P);
@@ -421,11 +446,20 @@ void build_patches(Host &h, int C, int P)
                         ring.push_back(o);
                     }
             }
+        // gather entries of the patch cells: {other, face, type, slot of other}
         for (int c = cb; c < ce; ++c)
             for (int e = h.cf_ptr[c]; e < h.cf_ptr[c + 1]; ++e) {
-                const int f = h.cf_face[e];
-                h.cf_sL[e] = (short)slot_of[h.fL[f]];
-                h.cf_sR[e] = (short)(h.fR[f] >= 0 ? slot_of[h.fR[f]] : -1);
+                const int f = h.cf_face[e], t = h.ftype[f];
+                int *g = &h.gi[(size_t)e * 4];
+                if (t == UGKS_FACE_INTERIOR || t == UGKS_FACE_PERIODIC) {
+                    const int o = h.cf_side[e] == 0 ? h.fR[f] : h.fL[f];
+                    g[0] = o;
+                    g[3] = slot_of[o];
+                } else {
+                    g[0] = h.faux[f];
+                }
+                g[1] = f;
+                g[2] = t;
             }
         h.max_slope = std::max(h.max_slope, ns);
         h.ring_cells.insert(h.ring_cells.end(), ring.begin(), ring.end());
@@ -571,8 +605,8 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     dc.cf_r_d = c->upload(h.cf_r);
     dc.cf_r = c->upload(cast<T>(h.cf_r));
     dc.cf_coef = c->upload(cast<T>(h.cf_coef));
-    dc.cf_sL = c->upload(h.cf_sL);
-    dc.cf_sR = c->upload(h.cf_sR);
+    dc.gi = reinterpret_cast<const int4 *>(c->upload(h.gi));
+    dc.gf = c->upload(cast<T>(h.gf));
     dc.eps2_d = c->upload(h.eps2);
     dc.eps2 = c->upload(cast<T>(h.eps2));
     dc.fL = c->upload(h.fL);
@@ -622,7 +656,8 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     const int NS = M * (M + 1) / 2;
     dc.fsum2 = (double *)c->dalloc(Fm * NS * (D + 1) * sizeof(double));
     dc.fprim0 = (double *)c->dalloc(Fm * M * sizeof(double));
-    dc.dW_part = (double *)c->dalloc((size_t)c->C * c->n_vt * M * sizeof(double));
+    // sized for the smallest velocity tile, so that the autotuner may retile
+    dc.dW_part = (double *)c->dalloc((size_t)c->C * (c->nvp / 32) * M * sizeof(double));
     dc.res_part = (double *)c->dalloc((size_t)c->n_res_blocks * 2 * M * sizeof(double));
     dc.flags = c->flags_d;
     dc.P = c->P;
@@ -637,78 +672,90 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
 
 namespace {
 
-// Autotuner of the gather tiling: the patch size is chosen by timing the gather
-// kernel itself on this case (it writes only f~ and scratch, so the state is
-// untouched), and the choice is cached per (dimension, precision, velocity
-// tile, velocity count, mesh-size bucket) for later cases of the same shape.
+// Autotuner of the gather tiling: the patch size and the velocity tile are
+// chosen by timing the gather kernel itself on this case (it writes only f~
+// and scratch, so the state is untouched), and the choice is cached per
+// (dimension, precision, velocity count, mesh-size bucket) for later cases of
+// the same shape.
 std::mutex g_tune_mutex;
-std::map<std::string, int> g_tune_cache;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
+
+// velocity tile used when neither the caller nor the autotuner sets one
+int kDefaultVtile(int prec) { return prec == UGKS_FP64 ? 32 : 64; }
 
 template <typename T>
-void set_patches(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, size_t smem)
+void set_tiling(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, int vtile, size_t smem)
 {
     c->P = P;
     c->n_patches = (int)((c->C + P - 1) / P);
+    c->vtile = vtile;
+    c->n_vt = (int)(c->nvp / vtile);
     c->cfg.smem = smem;
     dc.P = P;
     dc.n_patches = c->n_patches;
+    dc.vtile = vtile;
+    dc.n_vt = c->n_vt;
     dc.ring_ptr = c->upload(h.ring_ptr);
     dc.ring_cells = c->upload(h.ring_cells);
-    dc.cf_sL = c->upload(h.cf_sL);
-    dc.cf_sR = c->upload(h.cf_sR);
+    dc.gi = reinterpret_cast<const int4 *>(c->upload(h.gi));
 }
 
 template <typename T>
-void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max)
+void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tune_vtile)
 {
     const size_t esz = sizeof(T);
     char key[160];
-    snprintf(key, sizeof(key), "D%d_nc%d_p%d_vt%d_nv%lld_c%d", c->D, c->NC, c->prec, c->vtile, (long long)c->Nv,
-             (int)std::lround(std::log2((double)c->C)));
-    int best = 0;
+    snprintf(key, sizeof(key), "D%d_nc%d_p%d_vt%d_nv%lld_c%d", c->D, c->NC, c->prec, tune_vtile ? 0 : c->vtile,
+             (long long)c->Nv, (int)std::lround(std::log2((double)c->C)));
+    std::pair<int, int> best(0, 0);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) best = it->second;
     }
     const int C = (int)c->C;
-    auto smem_of = [&](const Host &hh) { return (size_t)hh.max_slope * c->NC * c->D * c->vtile * esz; };
-    if (best == 0) {
-        const std::vector<int> cand = c->prec == UGKS_FP64 ? std::vector<int>{16, 24, 32, 48}
-                                                           : std::vector<int>{32, 48, 64, 96};
+    auto smem_of = [&](const Host &hh, int vt) { return (size_t)hh.max_slope * c->NC * c->D * vt * esz; };
+    if (best.first == 0) {
+        const std::vector<int> pc = c->prec == UGKS_FP64 ? std::vector<int>{16, 24, 32, 48}
+                                                         : std::vector<int>{24, 32, 48, 64, 96};
+        std::vector<int> vc = {c->vtile};
+        if (tune_vtile) vc = {32, 64};
         cuda_ok(ugks::launch_pre_gather(dc, c->stream), "autotune prep");
         cudaEvent_t e0, e1;
         cuda_ok(cudaEventCreate(&e0), "event");
         cuda_ok(cudaEventCreate(&e1), "event");
         float best_ms = 0.f;
-        for (int P : cand) {
-            if (P > C && P != cand.front()) continue;
-            build_patches(h, C, P);
-            const size_t smem = smem_of(h);
-            if (smem > (size_t)smem_max) continue;
-            set_patches(c, dc, h, P, smem);
-            cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
-            cuda_ok(cudaEventRecord(e0, c->stream), "event");
-            for (int r = 0; r < 2; ++r) cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
-            cuda_ok(cudaEventRecord(e1, c->stream), "event");
-            cuda_ok(cudaEventSynchronize(e1), "event");
-            float ms = 0.f;
-            cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "event");
-            if (best == 0 || ms < best_ms) {
-                best = P;
-                best_ms = ms;
+        for (int vt : vc) {
+            if (c->nvp % vt) continue;
+            for (int P : pc) {
+                if (P > C && P != pc.front()) continue;
+                build_patches(h, C, P);
+                const size_t smem = smem_of(h, vt);
+                if (smem > (size_t)smem_max) continue;
+                set_tiling(c, dc, h, P, vt, smem);
+                cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
+                cuda_ok(cudaEventRecord(e0, c->stream), "event");
+                for (int r = 0; r < 2; ++r) cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
+                cuda_ok(cudaEventRecord(e1, c->stream), "event");
+                cuda_ok(cudaEventSynchronize(e1), "event");
+                float ms = 0.f;
+                cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "event");
+                if (best.first == 0 || ms < best_ms) {
+                    best = {P, vt};
+                    best_ms = ms;
+                }
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        if (best == 0) return;                       // keep the default tiling
+        if (best.first == 0) return;                 // keep the default tiling
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune_cache[key] = best;
     }
-    if (best != c->P) {
-        build_patches(h, C, best);
-        const size_t smem = smem_of(h);
-        if (smem <= (size_t)smem_max) set_patches(c, dc, h, best, smem);
+    if (best.first != c->P || best.second != c->vtile) {
+        build_patches(h, C, best.first);
+        const size_t smem = smem_of(h, best.second);
+        if (smem <= (size_t)smem_max) set_tiling(c, dc, h, best.first, best.second, smem);
     }
 }
 
@@ -775,7 +822,10 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         }
         const size_t esz = c->prec == UGKS_FP64 ? 8 : 4;
         // tiling: velocity tile of 32*TV, patch of P cells sized to shared memory
-        c->vtile = params->vtile > 0 ? params->vtile : 32;
+        // velocity rows are padded to a multiple of 64 unless the tile is fixed,
+        // so that the autotuner may choose a tile of 32 or 64 velocities
+        c->vtile = params->vtile > 0 ? params->vtile : kDefaultVtile(c->prec);
+        const int vpad = params->vtile > 0 ? params->vtile : 64;
         int P = params->patch_cells > 0 ? params->patch_cells : (c->prec == UGKS_FP64 ? 32 : 48);
         Host h;
         int dev = 0;
@@ -795,7 +845,7 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         }
         c->P = P;
         c->n_patches = (int)((c->C + P - 1) / P);
-        c->nvp = (c->Nv + c->vtile - 1) / c->vtile * c->vtile;
+        c->nvp = (c->Nv + vpad - 1) / vpad * vpad;
         c->n_vt = (int)(c->nvp / c->vtile);
         c->G = (int)h.gface.size();
         c->NW = (int)h.wface.size();
@@ -819,11 +869,11 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         if (c->prec == UGKS_FP64) {
             fill_case<double>(c.get(), c->d64, mesh, vgrid, params, h);
             cuda_ok(ugks::launch_init(c->d64, c->stream), "init");
-            if (params->patch_cells == 0) autotune<double>(c.get(), c->d64, h, smem_max);
+            if (params->patch_cells == 0) autotune<double>(c.get(), c->d64, h, smem_max, params->vtile == 0);
         } else {
             fill_case<float>(c.get(), c->d32, mesh, vgrid, params, h);
             cuda_ok(ugks::launch_init(c->d32, c->stream), "init");
-            if (params->patch_cells == 0) autotune<float>(c.get(), c->d32, h, smem_max);
+            if (params->patch_cells == 0) autotune<float>(c.get(), c->d32, h, smem_max, params->vtile == 0);
         }
         cuda_ok(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "create sync");
     });
@@ -1031,13 +1081,17 @@ ugks_status ugks_info(const ugks_case *c, ugks_info_t *info)
 
 struct ugks_batch {
     std::vector<ugks_case *> cases;
-    int D = 0, prec = 0, vtile = 0;
+    int D = 0, prec = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void *dcases = nullptr;         // device array of DevCase<T>
-    int4 *work = nullptr;
-    int nwork = 0, grid = 0;
-    size_t smem = 0;
+    // one persistent gather launch per velocity tile present in the batch
+    struct Group {
+        int vtile = 0, nwork = 0, grid = 0;
+        int4 *work = nullptr;
+        size_t smem = 0;
+    };
+    std::vector<Group> groups;
     static constexpr int NB = 8;    // parallel branches for the per-case kernels
     cudaStream_t br[NB] = {};
     cudaEvent_t fork = nullptr, fork2 = nullptr, join[NB] = {}, join2[NB] = {};
@@ -1061,28 +1115,35 @@ void batch_build(ugks_batch *b)
 {
     const int n = (int)b->cases.size();
     std::vector<ugks::DevCase<T>> h(n);
-    size_t smem = 0;
-    std::vector<int4> work;
-    int max_vt = 0;
-    for (int i = 0; i < n; ++i) {
-        h[i] = dc_of<T>(b->cases[i]);
-        smem = std::max(smem, b->cases[i]->cfg.smem);
-        max_vt = std::max(max_vt, b->cases[i]->n_vt);
-    }
-    // velocity tile outer, case, then patch innermost: consecutive CTAs work on
-    // neighbouring patches of one case and tile, as in the single-case grid
-    for (int vt = 0; vt < max_vt; ++vt)
-        for (int i = 0; i < n; ++i) {
-            if (vt >= b->cases[i]->n_vt) continue;
-            for (int pi = 0; pi < b->cases[i]->n_patches; ++pi) work.push_back(make_int4(i, pi, vt, 0));
-        }
+    for (int i = 0; i < n; ++i) h[i] = dc_of<T>(b->cases[i]);
     cuda_ok(cudaMalloc(&b->dcases, sizeof(ugks::DevCase<T>) * n), "batch alloc");
     cuda_ok(cudaMemcpy(b->dcases, h.data(), sizeof(ugks::DevCase<T>) * n, cudaMemcpyHostToDevice), "batch upload");
-    cuda_ok(cudaMalloc((void **)&b->work, sizeof(int4) * std::max<size_t>(1, work.size())), "batch alloc");
-    cuda_ok(cudaMemcpy(b->work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice), "batch upload");
-    b->nwork = (int)work.size();
-    b->smem = smem;
-    b->grid = std::min(b->nwork, ugks::gather_resident_ctas<T>(b->D, b->vtile, smem));
+    std::vector<int> tiles;
+    for (auto *c : b->cases)
+        if (std::find(tiles.begin(), tiles.end(), c->vtile) == tiles.end()) tiles.push_back(c->vtile);
+    for (int vtile : tiles) {
+        ugks_batch::Group g;
+        g.vtile = vtile;
+        std::vector<int4> work;
+        int max_vt = 0;
+        for (int i = 0; i < n; ++i)
+            if (b->cases[i]->vtile == vtile) {
+                g.smem = std::max(g.smem, b->cases[i]->cfg.smem);
+                max_vt = std::max(max_vt, b->cases[i]->n_vt);
+            }
+        // velocity tile outer, case, then patch innermost: consecutive CTAs work
+        // on neighbouring patches of one case and tile, as in the single-case grid
+        for (int vt = 0; vt < max_vt; ++vt)
+            for (int i = 0; i < n; ++i) {
+                if (b->cases[i]->vtile != vtile || vt >= b->cases[i]->n_vt) continue;
+                for (int pi = 0; pi < b->cases[i]->n_patches; ++pi) work.push_back(make_int4(i, pi, vt, 0));
+            }
+        cuda_ok(cudaMalloc((void **)&g.work, sizeof(int4) * std::max<size_t>(1, work.size())), "batch alloc");
+        b->groups.push_back(g);      // owned by the batch from here on
+        cuda_ok(cudaMemcpy(g.work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice), "batch upload");
+        b->groups.back().nwork = (int)work.size();
+        b->groups.back().grid = std::min((int)work.size(), ugks::gather_resident_ctas<T>(b->D, vtile, g.smem));
+    }
 }
 
 template <typename T>
@@ -1098,9 +1159,10 @@ void batch_capture(ugks_batch *b)
         cuda_ok(cudaEventRecord(b->join[k], b->br[k]), "join");
         cuda_ok(cudaStreamWaitEvent(st, b->join[k], 0), "join wait");
     }
-    cuda_ok(ugks::launch_gather_batch<T>(b->D, b->vtile, (const ugks::DevCase<T> *)b->dcases, b->work, b->nwork,
-                                         b->grid, b->smem, st),
-            "batched gather");
+    for (const auto &g : b->groups)
+        cuda_ok(ugks::launch_gather_batch<T>(b->D, g.vtile, (const ugks::DevCase<T> *)b->dcases, g.work, g.nwork,
+                                             g.grid, g.smem, st),
+                "batched gather");
     cuda_ok(cudaEventRecord(b->fork2, st), "fork");
     for (int k = 0; k < ugks_batch::NB; ++k) cuda_ok(cudaStreamWaitEvent(b->br[k], b->fork2, 0), "fork wait");
     for (size_t i = 0; i < b->cases.size(); ++i) {
@@ -1121,7 +1183,8 @@ void batch_free(ugks_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->dcases) cudaFree(b->dcases);
-    if (b->work) cudaFree(b->work);
+    for (auto &g : b->groups)
+        if (g.work) cudaFree(g.work);
     for (int k = 0; k < ugks_batch::NB; ++k) {
         if (b->br[k]) cudaStreamDestroy(b->br[k]);
         if (b->join[k]) cudaEventDestroy(b->join[k]);
@@ -1151,15 +1214,14 @@ ugks_status ugks_batch_create(ugks_case *const *cases, int32_t n, void *stream, 
         if (!cases || n <= 0) fail(UGKS_EINVAL, "a batch needs at least one case");
         for (int i = 0; i < n; ++i) {
             if (!cases[i]) fail(UGKS_EINVAL, "case %d is NULL", i);
-            if (cases[i]->D != cases[0]->D || cases[i]->prec != cases[0]->prec || cases[i]->vtile != cases[0]->vtile)
-                fail(UGKS_EINVAL, "case %d differs from case 0 in dimension, precision or velocity tile", i);
+            if (cases[i]->D != cases[0]->D || cases[i]->prec != cases[0]->prec)
+                fail(UGKS_EINVAL, "case %d differs from case 0 in dimension or precision", i);
             for (int j = 0; j < i; ++j)
                 if (cases[j] == cases[i]) fail(UGKS_EINVAL, "case %d appears twice", i);
             b->cases.push_back(cases[i]);
         }
         b->D = cases[0]->D;
         b->prec = cases[0]->prec;
-        b->vtile = cases[0]->vtile;
         if (stream) {
             b->stream = (cudaStream_t)stream;
         } else {

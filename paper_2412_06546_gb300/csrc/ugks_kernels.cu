@@ -812,48 +812,51 @@ __global__ void __launch_bounds__(256) k_wall_sum(DevCase<T> dc)
 }
 
 // ------------------------------------------------------------ gather pass
-// One CTA per (patch of P consecutive cells, tile of V = 32*TV velocities).
+// One CTA per (patch of P consecutive cells, tile of V = 32*TV velocities);
+// lane l handles the TV consecutive velocities V*tile + TV*l + j.
 // Phase A: limited slopes of the patch cells and their face neighbours (ring)
 //          into shared memory, each computed once.
 // Phase B: per patch cell, the flux of every face (Eq. microscopicFlux with
-//          Eq. fullSolution; walls per Sec. 2.5), stage 1 (Eq. microS1) written
-//          to f_nxt, and the moments sum_k w psi_k R_k of the flux residual for
-//          the W update (Eq. macroscopicUpdata / macroscopicFlux).
+//          Eq. fullSolution; walls per Sec. 2.5) in the cell's own
+//          orientation, stage 1 (Eq. microS1) written to f_nxt, and the moments
+//          sum_k w psi_k R_k of the flux residual for the W update (Eq.
+//          macroscopicUpdata / macroscopicFlux).  The cell's own f and slopes
+//          stay in registers; every face entry is read once for all TV
+//          velocities of the lane.
 template <typename T, int D, int NC, int TV>
 __device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, const int vt, T *sg)
 {
     constexpr int V = 32 * TV;
     constexpr int M = D + 2;
-    const int k0 = vt * V;
+    using E = GEnt<D>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int kl = vt * V + TV * lane;
     const int cb = p * dc.P;
     const int npc = min(dc.P, dc.C - cb);
     const int rb = dc.ring_ptr[p], re = dc.ring_ptr[p + 1];
     const int nslope = npc + (re - rb);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const T *__restrict__ f = dc.f_cur;
-    const size_t rs = (size_t)NC * dc.nvp;
+    const int nvp = dc.nvp;
+    const size_t rs = (size_t)NC * nvp;
+    const T *__restrict__ fl = dc.f_cur + kl;
+    T *const sl = sg + TV * lane;               // this lane's column of the slope buffer
 
-    T u[TV][3];
+    T u[3][TV];
+    ldv<T, TV>(dc.u[0] + kl, u[0]);
+    ldv<T, TV>(dc.u[1] + kl, u[1]);
+    if (D == 3) ldv<T, TV>(dc.u[2] + kl, u[2]);
+    else
 #pragma unroll
-    for (int j = 0; j < TV; ++j) {
-        const int k = k0 + lane + 32 * j;
-        u[j][0] = dc.u[0][k];
-        u[j][1] = dc.u[1][k];
-        u[j][2] = D == 3 ? dc.u[2][k] : T(0);
-    }
+        for (int j = 0; j < TV; ++j) u[2][j] = T(0);
 
     // ---- phase A: slopes (Alg. 1 line 5)
     for (int s = warp; s < nslope; s += nwarps) {
         const int c = s < npc ? cb + s : dc.ring_cells[rb + s - npc];
+        T g[NC][D][TV], fi[NC][TV];
+        cell_slope_tv<T, D, NC, TV>(dc, fl, c, u, g, fi);
 #pragma unroll
-        for (int j = 0; j < TV; ++j) {
-            T g[NC][D];
-            cell_slope<T, D, NC>(dc, f, c, k0 + lane + 32 * j, u[j], g);
+        for (int m = 0; m < NC; ++m)
 #pragma unroll
-            for (int m = 0; m < NC; ++m)
-#pragma unroll
-                for (int d = 0; d < D; ++d) sg[((s * NC + m) * D + d) * V + lane + 32 * j] = g[m][d];
-        }
+            for (int d = 0; d < D; ++d) stv<T, TV>(sl + ((s * NC + m) * D + d) * V, g[m][d]);
     }
     __syncthreads();
 
@@ -862,124 +865,149 @@ __device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, c
     const T hdt2 = T(0.5) * dc.dtT * dc.dtT;
     for (int s = warp; s < npc; s += nwarps) {
         const int c = cb + s;
-        T R[TV][NC];
+        T fs[NC][TV], gs[NC][D][TV], R[NC][TV];
 #pragma unroll
-        for (int j = 0; j < TV; ++j)
+        for (int m = 0; m < NC; ++m) {
+            ldv<T, TV>(fl + (size_t)c * rs + (size_t)m * nvp, fs[m]);
 #pragma unroll
-            for (int m = 0; m < NC; ++m) R[j][m] = 0;
-        const int e0 = dc.cf_ptr[c], e1 = dc.cf_ptr[c + 1];
+            for (int d = 0; d < D; ++d) ldv_s<T, TV>(sl + ((s * NC + m) * D + d) * V, gs[m][d]);
+#pragma unroll
+            for (int j = 0; j < TV; ++j) R[m][j] = 0;
+        }
+        const int e0 = __ldg(dc.cf_ptr + c), e1 = __ldg(dc.cf_ptr + c + 1);
+#pragma unroll 4
         for (int e = e0; e < e1; ++e) {
-            const int fid = dc.cf_face[e];
-            const T coef = dc.cf_coef[e];
-            const int typ = dc.ftype[fid];
-            T n[D];
+            const int4 gi = __ldg(dc.gi + e);
+            T ge[E::LEN];
+            load_rec<E::LEN>(dc.gf + (size_t)e * E::LEN, ge);
+            const T cs = ge[E::CS];
+            T un[TV];
 #pragma unroll
-            for (int d = 0; d < D; ++d) n[d] = dc.fn[(size_t)fid * D + d];
-            if (typ == FT_WALL) {
-                const T *wr = dc.wrec + (size_t)dc.faux[fid] * GREC;
-                const int sl = dc.cf_sL[e];
-                T r[D];
-#pragma unroll
-                for (int d = 0; d < D; ++d) r[d] = dc.cf_r[(size_t)e * D + d];
+            for (int j = 0; j < TV; ++j) {
+                const T uj[3] = {u[0][j], u[1][j], u[2][j]};
+                un[j] = normal_velocity<T, D>(uj, ge + E::N);
+            }
+            if (gi.z == FT_WALL) {
+                T wr[GREC];
+                load_rec<GREC>(dc.wrec + (size_t)gi.x * GREC, wr);
 #pragma unroll
                 for (int j = 0; j < TV; ++j) {
-                    const int k = k0 + lane + 32 * j;
-                    const T un = normal_velocity<T, D>(u[j], n);
+                    const T uj[3] = {u[0][j], u[1][j], u[2][j]};
                     T F[NC];
-                    if (un > T(0)) {
+                    if (un[j] > T(0)) {
 #pragma unroll
                         for (int m = 0; m < NC; ++m) {
-                            T fin = f[(size_t)c * rs + (size_t)m * dc.nvp + k], ug = 0;
+                            T fin = fs[m][j], ug = 0;
 #pragma unroll
                             for (int d = 0; d < D; ++d) {
-                                const T gd = sg[((sl * NC + m) * D + d) * V + lane + 32 * j];
-                                fin += gd * r[d];
-                                ug += u[j][d] * gd;
+                                fin += gs[m][d][j] * ge[E::RS + d];
+                                ug += uj[d] * gs[m][d][j];
                             }
-                            F[m] = un * (dt * fin - hdt2 * ug);
+                            F[m] = un[j] * (dt * fin - hdt2 * ug);
                         }
                     } else {
-                        const T H = maxwell_h<T, D>(wr, u[j]);
-                        F[0] = un * dt * H;
-                        if (NC == 2) F[NC - 1] = un * dt * wr[GR_NB] * H;
+                        const T H = maxwell_h<T, D>(wr, uj);
+                        F[0] = un[j] * dt * H;
+                        if (NC == 2) F[NC - 1] = un[j] * dt * wr[GR_NB] * H;
                     }
 #pragma unroll
-                    for (int m = 0; m < NC; ++m) R[j][m] += coef * F[m];
+                    for (int m = 0; m < NC; ++m) R[m][j] += cs * F[m];
                 }
-            } else {
-                T fr[XREC];
-                load_rec<XREC>(dc.xrec + (size_t)fid * XREC, fr);
-                const int sL = dc.cf_sL[e], sR = dc.cf_sR[e];
-                const int cL = dc.fL[fid], cR = dc.fR[fid];
-                T rL[D], rR[D];
-#pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    rL[d] = dc.frL[(size_t)fid * D + d];
-                    rR[d] = typ == FT_FARFIELD ? T(0) : dc.frR[(size_t)fid * D + d];
-                }
+                continue;
+            }
+            T fr[XREC];
+            load_rec<XREC>(dc.xrec + (size_t)gi.y * XREC, fr);
+            if (gi.z == FT_FARFIELD) {
+                T gr[GREC];
+                load_rec<GREC>(dc.grec + (size_t)gi.x * GREC, gr);
 #pragma unroll
                 for (int j = 0; j < TV; ++j) {
-                    const int k = k0 + lane + 32 * j;
-                    const T un = normal_velocity<T, D>(u[j], n);
-                    T fup[NC], ugf[NC];
-                    const bool left = un > T(0);
-                    if (!left && typ == FT_FARFIELD) {
-                        const T *gr = dc.grec + (size_t)dc.faux[fid] * GREC;
-                        const T H = maxwell_h<T, D>(gr, u[j]);
-                        fup[0] = H;
-                        if (NC == 2) fup[NC - 1] = gr[GR_NB] * H;
-#pragma unroll
-                        for (int m = 0; m < NC; ++m) ugf[m] = 0;
-                    } else {
-                        const int slot = left ? sL : sR;
-                        const int cu = left ? cL : cR;
+                    const T uj[3] = {u[0][j], u[1][j], u[2][j]};
+                    T fup[NC], ugf[NC], F[NC];
+                    if (un[j] > T(0)) {
 #pragma unroll
                         for (int m = 0; m < NC; ++m) {
-                            T v = f[(size_t)cu * rs + (size_t)m * dc.nvp + k], ug = 0;
+                            T v = fs[m][j], ug = 0;
 #pragma unroll
                             for (int d = 0; d < D; ++d) {
-                                const T gd = sg[((slot * NC + m) * D + d) * V + lane + 32 * j];
-                                v += gd * (left ? rL[d] : rR[d]);
-                                ug += u[j][d] * gd;
+                                v += gs[m][d][j] * ge[E::RS + d];
+                                ug += uj[d] * gs[m][d][j];
                             }
                             fup[m] = v;
                             ugf[m] = ug;
                         }
-                    }
-                    T F[NC];
-                    interface_flux<T, D, NC>(fr, u[j], un, fup, ugf, F);
+                    } else {
+                        const T H = maxwell_h<T, D>(gr, uj);
+                        fup[0] = H;
+                        if (NC == 2) fup[NC - 1] = gr[GR_NB] * H;
 #pragma unroll
-                    for (int m = 0; m < NC; ++m) R[j][m] += coef * F[m];
+                        for (int m = 0; m < NC; ++m) ugf[m] = 0;
+                    }
+                    interface_flux<T, D, NC>(fr, uj, un[j], fup, ugf, F);
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) R[m][j] += cs * F[m];
                 }
+                continue;
+            }
+            // interior or periodic: the neighbour's f and slopes
+            T fo[NC][TV], go[NC][D][TV];
+            const T *so = sl + (size_t)gi.w * NC * D * V;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                ldv<T, TV>(fl + (size_t)gi.x * rs + (size_t)m * nvp, fo[m]);
+#pragma unroll
+                for (int d = 0; d < D; ++d) ldv_s<T, TV>(so + (m * D + d) * V, go[m][d]);
+            }
+#pragma unroll
+            for (int j = 0; j < TV; ++j) {
+                const T uj[3] = {u[0][j], u[1][j], u[2][j]};
+                const bool self = un[j] > T(0);
+                T fup[NC], ugf[NC], F[NC];
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    T v = self ? fs[m][j] : fo[m][j], ug = 0;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        const T gd = self ? gs[m][d][j] : go[m][d][j];
+                        v += gd * (self ? ge[E::RS + d] : ge[E::RO + d]);
+                        ug += uj[d] * gd;
+                    }
+                    fup[m] = v;
+                    ugf[m] = ug;
+                }
+                interface_flux<T, D, NC>(fr, uj, un[j], fup, ugf, F);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) R[m][j] += cs * F[m];
             }
         }
         // stage 1 and the moments of R
-        const T *cr = dc.crec + (size_t)c * CREC;
+        T cr[CREC];
+        load_rec<CREC>(dc.crec + (size_t)c * CREC, cr);
         const T cc = cr[CR_C];
+        T wk[TV];
+        ldv<T, TV>(dc.w + kl, wk);
         T mom[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) mom[i] = 0;
+        T out[NC][TV];
 #pragma unroll
         for (int j = 0; j < TV; ++j) {
-            const int k = k0 + lane + 32 * j;
+            const T uj[3] = {u[0][j], u[1][j], u[2][j]};
             T fp[NC];
-            shakhov_fplus<T, D, NC>(cr, u[j], fp);
+            shakhov_fplus<T, D, NC>(cr, uj, fp);
 #pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                const size_t o = (size_t)c * rs + (size_t)m * dc.nvp + k;
-                const T fc = f[o];
-                dc.f_nxt[o] = fc + R[j][m] + cc * (fp[m] - fc);
-            }
-            const T wk = dc.w[k];
+            for (int m = 0; m < NC; ++m) out[m][j] = fs[m][j] + R[m][j] + cc * (fp[m] - fs[m][j]);
             T u2 = 0;
 #pragma unroll
-            for (int d = 0; d < D; ++d) u2 += u[j][d] * u[j][d];
-            const T wr0 = wk * R[j][0];
+            for (int d = 0; d < D; ++d) u2 += uj[d] * uj[d];
+            const T wr0 = wk[j] * R[0][j];
             mom[0] += wr0;
 #pragma unroll
-            for (int d = 0; d < D; ++d) mom[1 + d] += u[j][d] * wr0;
-            mom[D + 1] += T(0.5) * (u2 * wr0 + (NC == 2 ? wk * R[j][NC - 1] : T(0)));
+            for (int d = 0; d < D; ++d) mom[1 + d] += uj[d] * wr0;
+            mom[D + 1] += T(0.5) * (u2 * wr0 + (NC == 2 ? wk[j] * R[NC - 1][j] : T(0)));
         }
+#pragma unroll
+        for (int m = 0; m < NC; ++m) stv<T, TV>(dc.f_nxt + kl + (size_t)c * rs + (size_t)m * nvp, out[m]);
         constexpr int NR = M <= 4 ? 4 : 8;
         T red[NR];
 #pragma unroll

@@ -69,6 +69,7 @@ size_t footprint_estimate(const Request &r)
     b += C * 2 * 12 * s + C * (nvp / 32 + 1) * M * 8;                  // records, residual partials
     b += F * (size_t)(40 * s + 24 * s + 16 * s + (D * M + D + D + M + M) * 8 + 60 * 8 + 64);
     b += 2 * F * (size_t)(8 * D + 24) + C * 64 + nvp * 64;             // geometry, LSQ, patches
+    b += 2 * F * (size_t)(16 + 16 * s);                                // gather entries
     b += (size_t)64 * 256 * 40;                                        // allocation rounding
     return b + b / 8;
 }
@@ -135,6 +136,9 @@ ugks_status create_case(ugks_server *s, Request *r)
     p.wall_T = r->wall_T.empty() ? nullptr : r->wall_T.data();
     p.wall_U = r->wall_U.empty() ? nullptr : r->wall_U.data();
     p.prim_init = r->has_init ? r->prim_init.data() : nullptr;
+    // one velocity tile for every case of a precision, so that all of them
+    // share one batched gather launch
+    if (p.vtile == 0) p.vtile = p.precision == UGKS_FP64 ? 32 : 64;
     return ugks_create(&m, &v, &p, nullptr, (void *)s->stream, &r->c);
 }
 
@@ -284,8 +288,7 @@ ugks_status ugks_server_tick(ugks_server *s, int32_t *n_running, int32_t *n_queu
             for (Request *r : s->running) {
                 ugks_info_t inf;
                 ugks_info(r->c, &inf);
-                groups[std::to_string(inf.dim) + "/" + std::to_string(inf.precision) + "/" + std::to_string(inf.vtile)]
-                    .push_back(r->c);
+                groups[std::to_string(inf.dim) + "/" + std::to_string(inf.precision)].push_back(r->c);
             }
             for (auto &g : groups) {
                 ugks_batch *b = nullptr;

@@ -1,6 +1,7 @@
 """Batched stepping (ugks_batch_*): cases of different meshes and velocity
-grids stepped together in one persistent gather launch per step, captured as a
-CUDA graph, give bit-identical results to stepping each case alone."""
+grids stepped together with one persistent gather launch per velocity-tile
+width, captured as a CUDA graph, give bit-identical results to stepping each
+case alone."""
 import numpy as np
 import pytest
 
@@ -60,6 +61,25 @@ def test_batch_3d_and_interleaving_with_single_steps():
     b.step(2)
     for a, t in zip(alone, mixed):
         assert np.array_equal(a.state()[0], t.state()[0])
+
+
+def test_batch_with_mixed_velocity_tiles():
+    """Cases tiled with 32, 64 and 128 velocities per CTA in one batch (one
+    persistent launch per tile width) match the same cases stepped alone."""
+    specs = _cases2d()[:3]
+    tiles = [(24, 32), (48, 64), (16, 128)]
+    mk = lambda c, t: _lib.Case(c["mesh"], c["vgrid"], c["params"], c["init"], precision=_lib.FP32,
+                                patch_cells=t[0], vtile=t[1])
+    alone = [mk(c, t) for c, t in zip(specs, tiles)]
+    for g in alone:
+        g.step(4)
+    together = [mk(c, t) for c, t in zip(specs, tiles)]
+    b = _lib.Batch(together)
+    b.step(4)
+    for a, t in zip(alone, together):
+        assert np.array_equal(a.state()[0], t.state()[0])
+        assert np.array_equal(a.residual(), t.residual())
+    b.close()
 
 
 def test_batch_rejects_mixed_precision():
