@@ -152,6 +152,14 @@ ugks_status ugks_residual(ugks_case *c, double *res);
  * W[C][dim+2] (conserved variables); either may be NULL.  Synchronises. */
 ugks_status ugks_get_state(ugks_case *c, double *f, double *W);
 
+/* The state of selected cells only: for i < n, f[i][ncomp][nv] (FP64) and
+ * W[i][dim+2] of caller cell cells[i] (either output may be NULL; ids may
+ * repeat).  Serves sampled checks of cases whose whole distribution would not
+ * fit host memory.  n <= n_cells.  UGKS_EINVAL for NULL cells, n out of range
+ * or an id outside [0, n_cells).  Uses the case's per-step scratch as staging
+ * (between steps only); synchronises. */
+ugks_status ugks_get_cells(ugks_case *c, const int64_t *cells, int64_t n, double *f, double *W);
+
 /* Replace the state from host buffers (same layout); either may be NULL.
  * The heat flux is recomputed from the new f.  Asynchronous with respect to
  * the host after the upload is issued. */

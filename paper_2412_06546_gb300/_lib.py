@@ -92,6 +92,7 @@ EXPORTS = {
     "ugks_residual": (ct.c_int, [ct.c_void_p, D_P]),
     "ugks_get_state": (ct.c_int, [ct.c_void_p, D_P, D_P]),
     "ugks_set_state": (ct.c_int, [ct.c_void_p, D_P, D_P]),
+    "ugks_get_cells": (ct.c_int, [ct.c_void_p, I64_P, ct.c_int64, D_P, D_P]),
     "ugks_info": (ct.c_int, [ct.c_void_p, ct.POINTER(Info)]),
     "ugks_profile_begin": (ct.c_int, [ct.c_void_p, ct.c_int32]),
     "ugks_profile_end": (ct.c_int, [ct.c_void_p, D_P, ct.c_int32, ct.POINTER(ct.c_int32)]),
@@ -259,6 +260,14 @@ class Case:
         f = np.empty((self.C, self.nc, self.Nv)) if with_f else None
         W = np.empty((self.C, self.D + 2))
         check(load().ugks_get_state(self._h, _p(f), _p(W)))
+        return f, W
+
+    def cells(self, ids, with_f=True):
+        """f [n][ncomp][nv] and W [n][dim+2] of the caller cells ``ids``."""
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        f = np.empty((len(ids), self.nc, self.Nv)) if with_f else None
+        W = np.empty((len(ids), self.D + 2))
+        check(load().ugks_get_cells(self._h, ids.ctypes.data_as(I64_P), len(ids), _p(f), _p(W)))
         return f, W
 
     def set_state(self, f=None, W=None):

@@ -61,6 +61,7 @@ struct ugks_case {
     ugks::StepConfig cfg{};
     int P = 0, vtile = 0, n_patches = 0, n_vt = 0;
     long long *perm_d = nullptr;   // caller cell i -> internal cell
+    std::vector<long long> perm_h; // the same on the host
     double *res_d = nullptr;       // [M]
     int *flags_d = nullptr;
     int n_res_blocks = 0;
@@ -864,8 +865,8 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         cuda_ok(cudaMemsetAsync(c->flags_d, 0, sizeof(int), c->stream), "memset");
         c->res_d = (double *)c->dalloc(8 * sizeof(double));
         cuda_ok(cudaMemsetAsync(c->res_d, 0, 8 * sizeof(double), c->stream), "memset");
-        std::vector<long long> perm(h.perm_u2i.begin(), h.perm_u2i.end());
-        c->perm_d = c->upload(perm);
+        c->perm_h.assign(h.perm_u2i.begin(), h.perm_u2i.end());
+        c->perm_d = c->upload(c->perm_h);
         if (c->prec == UGKS_FP64) {
             fill_case<double>(c.get(), c->d64, mesh, vgrid, params, h);
             cuda_ok(ugks::launch_init(c->d64, c->stream), "init");
@@ -989,6 +990,51 @@ ugks_status ugks_get_state(ugks_case *c, double *f, double *W)
                 });
             }
         }
+    });
+}
+
+ugks_status ugks_get_cells(ugks_case *c, const int64_t *cells, int64_t n, double *f, double *W)
+{
+    return guard([&] {
+        if (!c || !cells) fail(UGKS_EINVAL, "case and cells must not be NULL");
+        if (n < 0 || n > c->C) fail(UGKS_EINVAL, "n = %lld outside [0, n_cells]", (long long)n);
+        if (n == 0) return;
+        const int D = c->D, M = D + 2;
+        std::vector<long long> ids((size_t)n);
+        for (int64_t i = 0; i < n; ++i) {
+            if (cells[i] < 0 || cells[i] >= c->C) fail(UGKS_EINVAL, "cell id %lld out of range", (long long)cells[i]);
+            ids[(size_t)i] = c->perm_h[(size_t)cells[i]];
+        }
+        // staging in the gradient scratch (C*D*M doubles >= n*(1 + M)): the
+        // internal ids, then W; f goes through the f~ buffer in chunks
+        double *gW = c->prec == UGKS_FP64 ? c->d64.gradW : c->d32.gradW;
+        long long *ids_d = reinterpret_cast<long long *>(gW);
+        double *wst = gW + n;
+        cuda_ok(cudaMemcpyAsync(ids_d, ids.data(), (size_t)n * sizeof(long long), cudaMemcpyHostToDevice, c->stream),
+                "ids upload");
+        if (W) {
+            double *Wd = c->prec == UGKS_FP64 ? c->d64.W : c->d32.W;
+            cuda_ok(ugks::launch_W_permute(Wd, ids_d, (int)n, D, wst, 0, c->stream), "W gather");
+            cuda_ok(cudaMemcpyAsync(W, wst, (size_t)n * M * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                    "W copy");
+        }
+        if (f) {
+            const size_t per = (size_t)c->NC * c->Nv;
+            const size_t cap = c->f_bytes / sizeof(double);
+            const int chunk = (int)std::max<size_t>(1, std::min<size_t>(cap / per, (size_t)n));
+            for (int c0 = 0; c0 < (int)n; c0 += chunk) {
+                const int nc = (int)std::min<int64_t>(chunk, n - c0);
+                with_dc(c, [&](auto &dc) {
+                    double *stg = (double *)dc.f_nxt;
+                    cuda_ok(ugks::launch_f_export(dc, ids_d, c0, nc, stg, c->stream), "f gather");
+                    cuda_ok(cudaMemcpyAsync(f + (size_t)c0 * per, stg, (size_t)nc * per * sizeof(double),
+                                            cudaMemcpyDeviceToHost, c->stream),
+                            "f copy");
+                });
+                cuda_ok(cudaStreamSynchronize(c->stream), "sync");
+            }
+        }
+        cuda_ok(cudaStreamSynchronize(c->stream), "sync");
     });
 }
 
