@@ -289,7 +289,7 @@ void or_moment_matrix(int32_t D, int64_t nv, const double *u, const double *w, c
     }
 }
 
-/* Interface equilibrium (Sec. 2.4; Alg. 1 line 3).
+/* Interface equilibrium (Sec. 2.4; the equilibrium step of Algorithm 1).
  * READING: g0 is the Maxwellian of W0, the conservative moments of the
  * particles arriving from both sides, computed before the velocity loop from
  * the macroscopic reconstruction: W0 = sum_k w_k psi_k [H(u_n) g_L + (1-H(u_n)) g_R]
@@ -518,7 +518,7 @@ or_case *or_create(const or_mesh *m, const or_vgrid *v, const or_params *p,
     }
     free(dvec);
 
-    /* READING (Alg. 1 line 1): the CFL condition of the upwind finite-volume
+    /* READING (the CFL condition of Algorithm 1): the stability bound of the upwind finite-volume
      * update, dt <= |Omega_i| / sum_f S_f (u_k . n_f)^+; since the positive
      * part is at most |u_k| sum_f S_f / 2, dt = CFL min_i (2 |Omega_i| /
      * sum_f S_f) / max_k |u_k| (= CFL h_i / (D max|u|)), fixed for a fixed
@@ -763,7 +763,7 @@ static void one_step(or_case *c)
 
     memcpy(c->Wold, c->W, sizeof(double) * C * M);
 
-    /* ---- Alg. 1 line 1: heat flux of each cell from f^n ---- */
+    /* ---- Algorithm 1: heat flux of each cell from f^n ---- */
 #pragma omp parallel for num_threads(nt) schedule(static)
     for (int64_t i = 0; i < C; ++i) {
         prim_of(D, c->W + i * M, &c->rho[i], c->U + i * D, &c->lam[i]);
@@ -794,7 +794,7 @@ static void one_step(or_case *c)
         }
     }
 
-    /* ---- Alg. 1 line 2: macroscopic reconstruction ----
+    /* ---- Algorithm 1: macroscopic reconstruction ----
      * READING: the "gradients of macroscopic values" are least-squares
      * gradients of the primitive variables (rho, U, T), and the "gradient
      * compressor factors" of the cited sliding-mesh paper are taken as
@@ -831,7 +831,7 @@ static void one_step(or_case *c)
         }
     }
 
-    /* ---- Alg. 1 line 3: interface equilibrium and time coefficients ---- */
+    /* ---- Algorithm 1: interface equilibrium and time coefficients ---- */
 #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
     for (int64_t f = 0; f < F; ++f) {
         int t = c->face_type[f];
@@ -864,7 +864,7 @@ static void one_step(or_case *c)
         for (int m = 0; m < M; ++m) c->Fm[f * M + m] = 0.0;
     }
 
-    /* ---- Alg. 1 lines 4-9: the velocity loop ---- */
+    /* ---- Algorithm 1: the velocity loop ---- */
     for (int64_t k = 0; k < Nv; ++k) {
         const double *uk = c->u + k * D;
         double u2 = 0.0;
@@ -880,14 +880,14 @@ static void one_step(or_case *c)
             if (nc == 2) c->ghost_k[f * nc + 1] = B;
         }
 
-        /* line 5: reconstruct f_k (limited, positivity-scaled slope per component) */
+        /* reconstruct f_k (limited, positivity-scaled slope per component) */
 #pragma omp parallel for num_threads(nt) schedule(static)
         for (int64_t i = 0; i < C; ++i)
             for (int cc = 0; cc < nc; ++cc)
                 micro_gradient(c, i, c->f + cc * Nv + k, (int64_t)nc * Nv, c->ghost_k + cc, nc, uk,
                                c->grad_k + (i * nc + cc) * D);
 
-        /* line 6: flux F_k through every non-wall face (Eq. microscopicFlux,
+        /* flux F_k through every non-wall face (Eq. microscopicFlux,
          * Eq. fullSolution) and its macroscopic contribution (Eq. macroscopicFlux) */
 #pragma omp parallel for num_threads(nt) schedule(static)
         for (int64_t f = 0; f < F; ++f) {
@@ -956,7 +956,7 @@ static void one_step(or_case *c)
             Fm[D + 1] += c->w[k] * 0.5 * (u2 * Fh + Fb);
         }
 
-        /* line 7: interpolate f_k and its gradient to the wall faces */
+        /* interpolate f_k and its gradient to the wall faces */
         for (int64_t s = 0; s < c->n_wall; ++s) {
             int64_t f = c->wall_face[s];
             int64_t i = c->face_cells[2 * f];
@@ -970,7 +970,7 @@ static void one_step(or_case *c)
             }
         }
 
-        /* line 8: stage 1 (Eq. microS1) over non-wall faces, in place */
+        /* stage 1 (Eq. microS1) over non-wall faces, in place */
 #pragma omp parallel for num_threads(nt) schedule(static)
         for (int64_t i = 0; i < C; ++i) {
             double H, B, Hp, Bp;
@@ -992,7 +992,7 @@ static void one_step(or_case *c)
         }
     }
 
-    /* ---- Alg. 1 line 10: flux at the walls (Sec. 2.5) ----
+    /* ---- Algorithm 1: flux at the walls (Sec. 2.5) ----
      * READING: outgoing particles (u_n > 0, n pointing into the wall) are
      * transported freely, f_in(-u t) = f_in - t u.grad f_in; incoming particles
      * carry g_w with rho_w from zero net mass flux (Eq. maxWalldes). */
@@ -1051,7 +1051,7 @@ static void one_step(or_case *c)
         }
     }
 
-    /* ---- Alg. 1 line 11: W update (Eq. macroscopicUpdata) ---- */
+    /* ---- Algorithm 1: W update (Eq. macroscopicUpdata) ---- */
 #pragma omp parallel for num_threads(nt) schedule(static)
     for (int64_t i = 0; i < C; ++i) {
         for (int m = 0; m < M; ++m) {
@@ -1065,7 +1065,7 @@ static void one_step(or_case *c)
         }
     }
 
-    /* ---- Alg. 1 line 12: stage 2 (Eq. microS2) with f+^{(n+1)} from W^{n+1}
+    /* ---- Algorithm 1: stage 2 (Eq. microS2) with f+^{(n+1)} from W^{n+1}
      * READING: the Shakhov heat flux of f+^{(n+1)} is the lagged q^n ---- */
 #pragma omp parallel for num_threads(nt) schedule(static)
     for (int64_t i = 0; i < C; ++i) {

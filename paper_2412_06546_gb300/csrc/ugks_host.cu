@@ -857,7 +857,7 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
                 for (int d = 0; d < c->D; ++d) s += vgrid->u[k * c->D + d] * vgrid->u[k * c->D + d];
                 umax = std::max(umax, std::sqrt(s));
             }
-            return params->cfl * h.hmin / umax;   // upwind CFL bound (Alg. 1 line 1)
+            return params->cfl * h.hmin / umax;   // upwind CFL bound (the CFL step of Algorithm 1)
         }();
         c->n_res_blocks = (int)((c->C + 255) / 256);
         c->cfg.n_res_blocks = c->n_res_blocks;

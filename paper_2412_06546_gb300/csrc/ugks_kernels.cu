@@ -848,7 +848,7 @@ __device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, c
 #pragma unroll
         for (int j = 0; j < TV; ++j) u[2][j] = T(0);
 
-    // ---- phase A: slopes (Alg. 1 line 5)
+    // ---- phase A: slopes (micro reconstruction of the velocity loop, Algorithm 1)
     for (int s = warp; s < nslope; s += nwarps) {
         const int c = s < npc ? cb + s : dc.ring_cells[rb + s - npc];
         T g[NC][D][TV], fi[NC][TV];
@@ -860,7 +860,7 @@ __device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, c
     }
     __syncthreads();
 
-    // ---- phase B: fluxes, stage 1, moments (Alg. 1 lines 6-8, 10)
+    // ---- phase B: fluxes, stage 1, moments (velocity loop and wall flux, Algorithm 1)
     const T dt = dc.dtT;
     const T hdt2 = T(0.5) * dc.dtT * dc.dtT;
     for (int s = warp; s < npc; s += nwarps) {
