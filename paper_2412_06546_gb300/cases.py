@@ -435,6 +435,224 @@ def sphere_mesh(n_target=150000, seed=3, r_in=1.0, r_out=12.0, ratio=1.08, tol=0
     return simplex_mesh(pts, simp.astype(np.int64), classify)
 
 
+# X38-like lifting body: a smooth convex superellipsoid of length 8 (x) and
+# span 3.5 (y), F(x) = |x/a|^px + |y/b|^py + |z/c|^pz <= 1 with the exponent
+# and semi-axis chosen per side: an ellipsoidal nose (x < 0) and a blunter aft
+# end (x > 0), a nearly flat bottom (z < 0, exponent 6) and a rounded top.
+_X38_SIDES = {"ax": (4.0, 4.0), "px": (2.0, 4.0), "b": 1.75, "py": 2.5, "cz": (0.6, 1.1), "pz": (6.0, 2.2)}
+
+
+def _x38_terms(X):
+    g = _X38_SIDES
+    x, y, z = X[..., 0], X[..., 1], X[..., 2]
+    ax = np.where(x < 0, g["ax"][0], g["ax"][1])
+    px = np.where(x < 0, g["px"][0], g["px"][1])
+    cz = np.where(z < 0, g["cz"][0], g["cz"][1])
+    pz = np.where(z < 0, g["pz"][0], g["pz"][1])
+    return (x, ax, px), (y, g["b"], g["py"]), (z, cz, pz)
+
+
+def x38_body_F(X):
+    """Implicit function of the X38-like body (< 1 inside, 1 on the surface)."""
+    return sum(np.abs(v / a) ** q for v, a, q in _x38_terms(np.asarray(X, float)))
+
+
+def _x38_normal(X):
+    gr = np.stack([q * np.sign(v) * np.abs(v) ** (q - 1) / a ** q for v, a, q in _x38_terms(X)], axis=-1)
+    return gr / np.linalg.norm(gr, axis=-1, keepdims=True)
+
+
+def _x38_surface(m, rng):
+    """m points on the body surface: directions of a Fibonacci lattice,
+    stretched to the body's proportions, projected along rays from the centre."""
+    d = _fibonacci_sphere(m, rng) * np.array([4.0, 1.75, 0.85])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    lo, hi = np.zeros(m), np.full(m, 8.0)
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        inside = x38_body_F(mid[:, None] * d) < 1.0
+        lo = np.where(inside, mid, lo)
+        hi = np.where(inside, hi, mid)
+    return 0.5 * (lo + hi)[:, None] * d
+
+
+def _thin(X, h, rng):
+    """Greedy thinning in random order: keep a point unless a kept point lies
+    within its spacing h (scalar or per point)."""
+    from scipy.spatial import cKDTree
+    tree = cKDTree(X)
+    hh = np.broadcast_to(np.asarray(h, float), (len(X),))
+    gone = np.zeros(len(X), bool)
+    keep = []
+    for i in rng.permutation(len(X)):
+        if gone[i]:
+            continue
+        keep.append(i)
+        gone[tree.query_ball_point(X[i], hh[i])] = True
+    return X[np.sort(np.asarray(keep, np.int64))]
+
+
+def x38_mesh(h0=0.0449, seed=5, s_out=8.0, ratio=1.1, n_surface=400000):
+    """Seeded tetrahedral mesh around the X38-like body.
+
+    Point layers lie on offset surfaces of the (convex) body at distances
+    s_k along the outward normals, with thickness h0 ratio^k; each layer is
+    thinned to a spacing equal to its thickness.  Delaunay tetrahedra whose
+    centroid lies inside the body are removed.  Boundary faces on the body are
+    walls (tag 0), those on the outermost offset surface (at s_out) far field.
+    The default h0 gives 1,051,276 cells (seed 5)."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    P0 = _x38_surface(n_surface, rng)
+    N0 = _x38_normal(P0)
+    pts, s, k = [], 0.0, 0
+    while True:
+        hk = h0 * ratio ** k
+        pts.append(_thin(P0 + s * N0, hk, rng))
+        if s >= s_out:
+            break
+        s = min(s + hk, s_out)
+        k += 1
+    pts = np.concatenate(pts)
+    simp = Delaunay(pts).simplices
+    P = pts[simp]
+    keep = x38_body_F(P.mean(axis=1)) > 1.0
+    vol = np.abs(np.linalg.det(P[keep][:, 1:] - P[keep][:, :1])) / 6.0
+    ok = vol > 1e-12 * vol.max()
+    simp = simp[keep][ok]
+
+    def classify(fx):
+        typ = np.where(x38_body_F(fx) < 4.0, WALL, FARFIELD).astype(np.int32)
+        return typ, np.zeros(len(fx), np.int32)
+
+    mesh = simplex_mesh(pts, simp.astype(np.int64), classify)
+    mesh["_surface"] = P0
+    return mesh
+
+
+def tet_ball_vgrid(n_target=4548, R=18.9, centres=((0.0, 0.0, 0.0),), h_min=0.6, grad=0.35, seed=5,
+                   tol=0.02):
+    """Unstructured 3D velocity grid: a seeded Delaunay tetrahedralisation of
+    the ball |u| <= R whose spacing grows from h_min at each of ``centres``
+    (h = min(h_min + grad d, R/4), d the distance to the nearest centre), with
+    the centroid rule (u_k = centroid, w_k = volume of cell k).  The spacing
+    scale is bisected to land near ``n_target`` cells."""
+    from scipy.spatial import Delaunay
+    C0 = np.asarray(centres, float)
+
+    def spacing(X, sc):
+        d = np.min(np.linalg.norm(X[:, None, :] - C0[None], axis=2), axis=1)
+        return sc * np.minimum(h_min + grad * d, R / 4.0)
+
+    def build(sc):
+        rng = np.random.default_rng(seed)
+        cand = rng.uniform(-R, R, size=(60000, 3))
+        cand = cand[np.linalg.norm(cand, axis=1) < R - 1e-9]
+        inner = _thin(cand, spacing(cand, sc), rng)
+        shell = R * _fibonacci_sphere(20000, rng)
+        shell = _thin(shell, spacing(shell, sc), rng)
+        if len(inner):
+            from scipy.spatial import cKDTree
+            d, _ = cKDTree(shell).query(inner)
+            inner = inner[d > 0.5 * spacing(inner, sc)]
+        X = np.concatenate([inner, shell])
+        tet = Delaunay(X).simplices
+        P = X[tet]
+        w = np.abs(np.linalg.det(P[:, 1:] - P[:, :1])) / 6.0
+        ok = w > 1e-12 * w.max()
+        return P[ok].mean(axis=1), w[ok]
+
+    lo, hi = 0.2, 5.0
+    u, w = build(1.0)
+    for _ in range(40):
+        mid = math.sqrt(lo * hi)
+        u, w = build(mid)
+        if abs(len(w) - n_target) <= tol * n_target:
+            break
+        if len(w) > n_target:
+            lo = mid
+        else:
+            hi = mid
+    return {"dim": 3, "u": np.ascontiguousarray(u), "w": np.ascontiguousarray(w), "cart_n": [0, 0, 0]}
+
+
+# ----------------------------------------------------------------------------
+# local problems: sampled checks and timings of cases too large for a whole
+# oracle run.  One explicit step updates a cell from data no further than two
+# face rings away: the limited slopes of the cell and of its face neighbours
+# (each reads its own neighbours' values), the interface equilibria of its
+# faces (face states of both sides, whose limited macroscopic gradients read
+# the second ring), the heat flux of both sides and, at walls, the cell's own
+# distribution.  A mesh made of the sample S0, S1 = S0 + face neighbours,
+# S2 = S1 + their face neighbours, with every face of every S1 cell, stepped
+# once from the same state on S2 with the same time step, therefore gives the
+# full-mesh step on S0.  Cells of S2 outside S1 lose faces and so get wrong
+# values of their own, which no S0 result reads.
+# ----------------------------------------------------------------------------
+def _adjacency(mesh):
+    fc = np.asarray(mesh["face_cells"])
+    ft = np.asarray(mesh["face_type"])
+    inner = (ft == INTERIOR) | (ft == PERIODIC)
+    a, b = fc[inner, 0], fc[inner, 1]
+    src = np.concatenate([a, b])
+    dst = np.concatenate([b, a])
+    order = np.argsort(src, kind="stable")
+    C = len(mesh["cell_vol"])
+    ptr = np.zeros(C + 1, np.int64)
+    np.add.at(ptr, src + 1, 1)
+    return np.cumsum(ptr), dst[order]
+
+
+def _grow(ptr, nb, cells):
+    return np.unique(np.concatenate([cells] + [nb[ptr[c]:ptr[c + 1]] for c in cells]))
+
+
+def local_problem(mesh, sample, rings=2):
+    """Return (sub-mesh, S2 cell ids in the full mesh, positions of the sample
+    cells in S2).  Sub-mesh faces keep the full mesh's face order.  ``rings``
+    < 2 builds a mesh that is too small (for the negative control)."""
+    sample = np.unique(np.asarray(sample, np.int64))
+    ptr, nb = _adjacency(mesh)
+    s1 = sample
+    for _ in range(rings - 1):
+        s1 = _grow(ptr, nb, s1)
+    s2 = _grow(ptr, nb, s1)
+    C = len(mesh["cell_vol"])
+    fc = np.asarray(mesh["face_cells"])
+    own, nei = fc[:, 0], fc[:, 1]
+    in1 = np.zeros(C, bool)
+    in1[s1] = True
+    faces = np.nonzero(in1[own] | ((nei >= 0) & in1[np.maximum(nei, 0)]))[0]
+    loc = -np.ones(C, np.int64)
+    loc[s2] = np.arange(len(s2))
+    o, n = own[faces], nei[faces]
+    sub_fc = np.stack([loc[o], np.where(n >= 0, loc[np.maximum(n, 0)], -1)], axis=1)
+    assert (sub_fc[:, 0] >= 0).all() and ((n < 0) | (sub_fc[:, 1] >= 0)).all()
+    sub = {"dim": mesh["dim"],
+           "cell_xc": np.ascontiguousarray(np.asarray(mesh["cell_xc"])[s2]),
+           "cell_vol": np.ascontiguousarray(np.asarray(mesh["cell_vol"])[s2]),
+           "face_cells": np.ascontiguousarray(sub_fc)}
+    for k in ("face_n", "face_S", "face_xc", "face_type", "face_tag", "face_shift"):
+        sub[k] = np.ascontiguousarray(np.asarray(mesh[k])[faces])
+    return sub, s2, loc[sample]
+
+
+def pick_sample(mesh, n, seed):
+    """Seeded sample of n cells: a quarter next to walls, a quarter next to the
+    far field (where the mesh has them), the rest anywhere."""
+    rng = np.random.default_rng(seed)
+    fc = np.asarray(mesh["face_cells"])
+    ft = np.asarray(mesh["face_type"])
+    C = len(mesh["cell_vol"])
+    picks = []
+    for t in (WALL, FARFIELD):
+        cand = np.unique(fc[ft == t, 0])
+        if len(cand):
+            picks.append(rng.choice(cand, size=min(len(cand), n // 4), replace=False))
+    picks.append(rng.choice(C, size=n - sum(len(p) for p in picks), replace=False))
+    return np.unique(np.concatenate(picks))
+
+
 # ----------------------------------------------------------------------------
 # parameter records and named workloads
 # ----------------------------------------------------------------------------
@@ -520,6 +738,36 @@ def sphere_case(n_cells=150000, nv=28, vmax=10.0, mach=4.0, Kn=0.1, seed=3, star
         init = blended_start(mesh, [Uinf, 0.0, 0.0])
     return {"name": f"sphere_Ma{mach:g}_Kn{Kn:g}_c{len(mesh['cell_vol'])}_v{nv}^3",
             "mesh": mesh, "vgrid": vg, "params": pr, "init": init}
+
+
+def x38_case(h0=0.0449, nv=4548, mach=8.0, Kn=0.005, aoa_deg=20.0, T_wall=302.0 / 56.0, seed=5,
+             start="blended"):
+    """3D Mach-8 argon flow past the X38-like body at 20 degrees angle of
+    attack (the flow meets the flat bottom), Kn 0.005 on the body length 8,
+    isothermal wall at T_w = 302/56 T_inf.  Velocities: ``nv`` tetrahedra in
+    the ball of radius 4 sqrt(T_s), T_s = 1 + (gamma - 1)/2 Ma^2 the
+    stagnation temperature, refined at rest and at U_inf (centroid rule)."""
+    mesh = x38_mesh(h0, seed=seed)
+    Uinf = freestream_speed(mach)
+    a = math.radians(aoa_deg)
+    Uv = [Uinf * math.cos(a), 0.0, Uinf * math.sin(a)]
+    Ts = 1.0 + (5.0 / 3.0 - 1.0) / 2.0 * mach * mach
+    vg = tet_ball_vgrid(nv, R=4.0 * math.sqrt(Ts), centres=((0.0, 0.0, 0.0), tuple(Uv)), seed=seed)
+    pr = params(Kn, L_ref=8.0, walls=[{"T": T_wall, "U": [0.0, 0.0, 0.0]}],
+                inf={"rho": 1.0, "U": Uv, "T": 1.0})
+    C = len(mesh["cell_vol"])
+    if start == "impulsive":
+        init = uniform_state(C, 3, U=Uv)
+    else:
+        # U rises from rest at the wall to the free stream with the distance d
+        # to the body surface: U(d) = U_inf (1 - exp(-d))
+        from scipy.spatial import cKDTree
+        d, _ = cKDTree(mesh["_surface"]).query(mesh["cell_xc"])
+        init = uniform_state(C, 3)
+        init[:, 1:4] = (1.0 - np.exp(-d))[:, None] * np.asarray(Uv)[None]
+    mesh.pop("_surface")
+    return {"name": f"x38_Ma{mach:g}_Kn{Kn:g}_c{C}_v{len(vg['w'])}", "mesh": mesh, "vgrid": vg,
+            "params": pr, "init": init}
 
 
 def perturbation(shape, seed, amp=0.1):

@@ -1,9 +1,10 @@
 """Sampled parity at the full workload sizes: the 30k-triangle Mach-5 cylinder
 (60x50 velocities) in the benchmark's launch configuration (FP32 storage,
-autotuned tiling) and the 147k-tetrahedron Mach-4 sphere (28^3 velocities) in
-both forms.  The GPU state on two face rings around seeded sample cells is
+autotuned tiling), the 147k-tetrahedron Mach-4 sphere (28^3 velocities) and
+the 1.05M-tetrahedron Mach-8 X38-like body (4,548 unstructured velocities)
+in both forms.  The GPU state on two face rings around seeded sample cells is
 read back with ugks_get_cells and stepped once by the oracle on the local
-problem (tests/_local.py, pinned on CPU by test_local_problem.py); the
+problem (cases.local_problem, pinned on CPU by test_local_problem.py); the
 oracle's result at the sample cells is compared element by element with the
 GPU's own step there.
 
@@ -21,7 +22,6 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from paper_2412_06546_gb300 import _lib, cases as cs  # noqa: E402
-from _local import local_problem, pick_sample  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -42,8 +42,8 @@ def _sampled(case, precision, n_sample, seed, steps_before=2, **tiling):
     mesh, vg, pr, init = case["mesh"], case["vgrid"], case["params"], case["init"]
     g = _lib.Case(mesh, vg, pr, init, precision=precision, **tiling)
     g.step(steps_before)
-    sample = pick_sample(mesh, n_sample, seed)
-    sub, s2, pos = local_problem(mesh, sample)
+    sample = cs.pick_sample(mesh, n_sample, seed)
+    sub, s2, pos = cs.local_problem(mesh, sample)
     fn, Wn = g.cells(s2)
     g.step(1)
     f1, W1 = g.cells(sample)
@@ -72,4 +72,19 @@ def test_sphere_full_size_fp32(sphere):
 
 def test_sphere_full_size_fp64(sphere):
     e = _sampled(sphere, _lib.FP64, 48, 13, patch_cells=16, vtile=32)
+    assert max(e.values()) <= 1e-12, e
+
+
+@pytest.fixture(scope="module")
+def x38():
+    return cs.x38_case()
+
+
+def test_x38_full_size_fp32(x38):
+    e = _sampled(x38, _lib.FP32, 48, 14)
+    assert e["f"] <= 1e-5 and e["f_l2"] <= 1e-5 and e["W"] <= 1e-5, e
+
+
+def test_x38_full_size_fp64(x38):
+    e = _sampled(x38, _lib.FP64, 48, 15, patch_cells=16, vtile=32)
     assert max(e.values()) <= 1e-12, e

@@ -7,7 +7,6 @@ import pytest
 
 import oracle
 from paper_2412_06546_gb300 import cases as cs
-from _local import local_problem, pick_sample
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -26,8 +25,8 @@ def _check(case, n_sample, seed, rings=2):
     full.step(1)
     f1, W1, _ = full.state()
 
-    sample = pick_sample(mesh, n_sample, seed)
-    sub, s2, pos = local_problem(mesh, sample, rings)
+    sample = cs.pick_sample(mesh, n_sample, seed)
+    sub, s2, pos = cs.local_problem(mesh, sample, rings)
     assert len(s2) < len(mesh["cell_vol"])
     params = dict(case["params"], dt=full.dt)
     loc = oracle.OracleCase(sub, case["vgrid"], params, np.asarray(case["init"])[s2], n_threads=0)
