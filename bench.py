@@ -104,6 +104,8 @@ def _workload(name):
     from paper_2412_06546_gb300 import cases
     if name == WORKLOAD:
         return cases.cylinder_case(n_cells=30000, nvx=60, nvy=50, mach=5.0, Kn=0.1, seed=2)
+    if name == "cylinder_Ma5_Kn0.1_tri8k_v60x50":       # the same flow on 8k cells (profiling captures)
+        return cases.cylinder_case(n_cells=8000, nvx=60, nvy=50, mach=5.0, Kn=0.1, seed=2)
     if name == "cavity20_v24":
         return cases.cavity_case()
     if name == "sphere_Ma4_Kn0.1_tet150k_v28":
@@ -143,6 +145,31 @@ def _max_over_ranks(torch, dist, v):
     t = torch.tensor([v], dtype=torch.float64, device="cuda")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _gather_traffic(workload, patch, vtile):
+    """DRAM bytes of one gather launch from the committed ncu summary, while
+    the gather's sources and tiling are those the counters were taken on
+    (else None: the kernel changed since)."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_gather_cylinder30k_fp32.md")
+    if workload != WORKLOAD or not os.path.exists(prof):
+        return None
+    h = hashlib.sha256()
+    for f in ("ugks_kernels.cu", "ugks_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2412_06546_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    fields = {}
+    for line in open(prof):
+        if ":" in line and line.split(":")[0] in ("gather-sources-sha256-16", "traffic-bytes-per-launch",
+                                                  "traffic-tiling"):
+            k, v = line.split(":", 1)
+            fields[k] = v.strip()
+    if fields.get("gather-sources-sha256-16") != h.hexdigest()[:16]:
+        return None
+    if fields.get("traffic-tiling") != f"patch {patch}, vtile {vtile}":
+        return None
+    return int(fields["traffic-bytes-per-launch"])
 
 
 def _cpu_baseline(case, steps=1, max_cvu=3e8):
@@ -359,7 +386,8 @@ def main():
                    "vtile": info["vtile"], "l2": f"inputs larger than L2 (f {info['f_bytes'] / 1e9:.2f} GB per copy)",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "kernel": "k_gather", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                     "traffic": _gather_traffic(args.workload, info["patch_cells"], info["vtile"]),
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": g_ms, "group_share": share},
         "fp64_plain": {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": fp64_steps,
