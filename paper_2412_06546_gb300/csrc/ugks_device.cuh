@@ -40,6 +40,9 @@ template <int D> struct Poly {
 
 enum { FT_INTERIOR = 0, FT_WALL = 1, FT_FARFIELD = 2, FT_PERIODIC = 3 };
 
+// nodes of the last velocity axis the separable half-range sums hold in shared memory
+constexpr int SUM1_SEP_MAX_NL = 512;
+
 // layout of the values of one gather entry (cell c, face f): a = LSQ
 // coefficient of the neighbour across f (0 for a wall), rs = x_f - x_c,
 // n = unit normal of f pointing out of c, ro = x_f - x_other (periodic image;
@@ -118,6 +121,8 @@ struct DevCase {
     int *flags;                   // [1] numeric failure flag
     // tensor-product velocity grid (sep = 1): axes and 1-D weights per dimension
     int sep, cart_n[3];
+    int sep1;                     // sep with the last axis strictly ascending and at most
+                                  // SUM1_SEP_MAX_NL nodes (separable half-range sums)
     const T *axis[3], *axw[3];
     // gather tiling
     int P, n_patches, n_vt, vtile;

@@ -513,6 +513,7 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     // w_k = wx_i wy_j [wz_l]; verified exactly for the axes and to 1e-14 for the
     // weights, else the general per-velocity face sums are used
     dc.sep = 0;
+    dc.sep1 = 0;
     for (int d = 0; d < 3; ++d) {
         dc.cart_n[d] = 0;
         dc.axis[d] = dc.axw[d] = nullptr;
@@ -558,6 +559,12 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
                     dc.axis[d] = c->upload(cast<T>(ax[d]));
                     dc.axw[d] = c->upload(cast<T>(aw[d]));
                 }
+                // the separable half-range sums search the last axis for the
+                // sign changes of u.n, so its nodes must ascend (also in T)
+                const std::vector<T> last = cast<T>(ax[D - 1]);
+                bool asc = last.size() <= (size_t)ugks::SUM1_SEP_MAX_NL;
+                for (size_t i = 1; i < last.size(); ++i) asc = asc && last[i - 1] < last[i];
+                dc.sep1 = asc ? 1 : 0;
             }
         }
     }

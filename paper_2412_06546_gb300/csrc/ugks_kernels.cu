@@ -1,16 +1,16 @@
 // ugks_kernels.cu -- the CUDA kernels of one UGKS time step (sm_103a).
 //
 // One step (Algorithm 1 of arXiv:2412.06546, reorganised for the GPU):
-//   k_prep        cell records from W^n, q^n; far-field ghost states     (Alg.1 l.1, Sec. 2.5)
-//   k_macro_grad  limited least-squares gradient of W                    (Alg.1 l.2)
-//   k_face_pre    face states W_L, W_R, interface macro gradient, q0     (Alg.1 l.3)
+//   k_prep        cell records from W^n, q^n; far-field ghost states     (CFL and heat-flux step, Sec. 2.5)
+//   k_macro_grad  limited least-squares gradient of W                    (macroscopic reconstruction)
+//   k_face_pre    face states W_L, W_R, interface macro gradient, q0     (interface equilibrium)
 //   k_face_sum1   half-range moments over the velocity grid -> W0        (Sec. 2.4)
 //   k_face_fin1   g0 parameters, tau0, time integrals q1..q5             (Sec. 2.4)
 //   k_face_sum2   moments of g0 for the slope systems                    (Sec. 2.4)
 //   k_face_fin2   spatial and time slopes of g0                          (Sec. 2.4)
 //   k_wall_sum    wall density from zero net mass flux                   (Eq. maxWalldes)
 //   k_gather      per (cell patch, velocity tile): micro slopes, face fluxes, stage 1,
-//                 moments of the flux residual                           (Alg.1 l.4-10, Eq. microS1)
+//                 moments of the flux residual                           (velocity loop, Eq. microS1)
 //   k_update_W    W^{n+1} and stage-2 coefficients                       (Eq. macroscopicUpdata)
 //   k_collide     stage 2 and the heat flux of f^{n+1}                   (Eq. microS2)
 // All per-velocity arithmetic is in T (double or float); moment sums are
@@ -387,6 +387,134 @@ __global__ void k_face_sum1(DevCase<T> dc)
     for (int m = 0; m < M; ++m) {
         T s = warp_sum(acc[m]);
         if (lane == 0) dc.fsum1[(size_t)f * M + m] = (double)s;
+    }
+}
+
+// k_face_sum1 on a tensor-product velocity grid.  With the face-state
+// Maxwellians factored by axis, the half-range sums become, for every point of
+// the outer axes, sums over a contiguous range of the last axis: u.n, rounded
+// as everywhere (no contraction, last term added last), is monotone along that
+// axis when its nodes ascend.  Prefix sums of the last axis' 1-D moments give
+// every range in O(1); the range ends come from binary searches on the exact
+// u.n, and nodes with u.n = 0 keep their half weight on both sides.  One warp
+// per face; the prefix sums live in shared memory, 2 sides x 3 powers x
+// (NL + 1) doubles per warp.
+constexpr int SUM1_SEP_WARPS = 4;
+
+template <typename T, int D, int NC>
+__global__ void __launch_bounds__(32 * SUM1_SEP_WARPS) k_face_sum1_sep(DevCase<T> dc)
+{
+    extern __shared__ __align__(16) unsigned char psum_raw[];
+    T *psum = reinterpret_cast<T *>(psum_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int f = blockIdx.x * SUM1_SEP_WARPS + warp;
+    constexpr int M = D + 2;
+    constexpr int L = D - 1;                 // the prefix-sum axis
+    const int NL = dc.cart_n[L];
+    if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
+    T *P = psum + (size_t)warp * 6 * (NL + 1);
+    const T *side[2] = {dc.fside + (size_t)f * 2 * GREC, dc.fside + (size_t)f * 2 * GREC + GREC};
+    T n[D], Ur[D];
+    for (int d = 0; d < D; ++d) {
+        n[d] = dc.fn[(size_t)f * D + d];
+        Ur[d] = (T)dc.fUref[(size_t)f * D + d];
+    }
+    // prefix sums over the last axis of w g (u - Ur)^p, p = 0, 1, 2, per side
+    for (int s = 0; s < 2; ++s) {
+        const T *r = side[s];
+        T *Ps = P + s * 3 * (NL + 1);
+        if (lane == 0) Ps[0] = Ps[NL + 1] = Ps[2 * (NL + 1)] = T(0);
+        T carry[3] = {0, 0, 0};
+        for (int j0 = 0; j0 < NL; j0 += 32) {
+            const int j = j0 + lane;
+            T v[3] = {0, 0, 0};
+            if (j < NL) {
+                const T a = dc.axis[L][j];
+                const T dv = a - r[GR_U + L];
+                const T g = dc.axw[L][j] * gauss<T>(r[GR_LAM], r[GR_NL2], dv * dv);
+                const T c = a - Ur[L];
+                v[0] = g;
+                v[1] = g * c;
+                v[2] = g * c * c;
+            }
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const T t = __shfl_up_sync(0xffffffffu, v[p], o);
+                    if (lane >= o) v[p] += t;
+                }
+                if (j < NL) Ps[p * (NL + 1) + j + 1] = carry[p] + v[p];
+                carry[p] += __shfl_sync(0xffffffffu, v[p], 31);
+            }
+        }
+    }
+    __syncwarp();
+    const T nl = n[L];
+    const T *aL = dc.axis[L];
+    int nouter = dc.cart_n[0];
+    if (D == 3) nouter *= dc.cart_n[1];
+    T acc[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] = 0;
+    for (int o = lane; o < nouter; o += 32) {
+        int idx[2] = {o % dc.cart_n[0], D == 3 ? o / dc.cart_n[0] : 0};
+        T uo[2];
+        uo[0] = dc.axis[0][idx[0]];
+        uo[1] = D == 3 ? dc.axis[1][idx[1]] : T(0);
+        T sp = mul_rn(uo[0], n[0]);
+        if (D == 3) sp = add_rn(sp, mul_rn(uo[1], n[1]));
+        // [ja, jb): u.n = 0; ascending u.n (nl >= 0): u.n < 0 on [0, ja), > 0 on [jb, NL);
+        // descending (nl < 0): u.n > 0 on [0, ja), < 0 on [jb, NL)
+        auto first = [&](int mode) {
+            int lo = 0, hi = NL;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const T v = add_rn(sp, mul_rn(aL[mid], nl));
+                const bool t = mode == 0 ? v >= T(0) : mode == 1 ? v > T(0) : mode == 2 ? v <= T(0) : v < T(0);
+                if (t) hi = mid;
+                else lo = mid + 1;
+            }
+            return lo;
+        };
+        const bool asc = nl >= T(0);
+        const int ja = first(asc ? 0 : 2), jb = first(asc ? 1 : 3);
+        T co2 = 0, co[2];
+#pragma unroll
+        for (int e = 0; e < D - 1; ++e) {
+            co[e] = uo[e] - Ur[e];
+            co2 += co[e] * co[e];
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const T *r = side[s];
+            const T *Ps = P + s * 3 * (NL + 1);
+            const bool lo_side = (s == 0) != asc;        // the full range starts at 0
+            const int f0 = lo_side ? 0 : jb, f1 = lo_side ? ja : NL;
+            T Y[3];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                const T *Pp = Ps + p * (NL + 1);
+                Y[p] = (Pp[f1] - Pp[f0]) + T(0.5) * (Pp[jb] - Pp[ja]);
+            }
+            T go = r[GR_PREF];
+#pragma unroll
+            for (int e = 0; e < D - 1; ++e) {
+                const T dv = uo[e] - r[GR_U + e];
+                go *= dc.axw[e][idx[e]] * gauss<T>(r[GR_LAM], r[GR_NL2], dv * dv);
+            }
+            const T g = go;
+            acc[0] += g * Y[0];
+#pragma unroll
+            for (int e = 0; e < D - 1; ++e) acc[1 + e] += g * co[e] * Y[0];
+            acc[1 + L] += g * Y[1];
+            acc[D + 1] += T(0.5) * g * (co2 * Y[0] + Y[2] + r[GR_NB] * Y[0]);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const T sm = warp_sum(acc[m]);
+        if (lane == 0) dc.fsum1[(size_t)f * M + m] = (double)sm;
     }
 }
 
@@ -1274,7 +1402,14 @@ static void pre_gather(const DevCase<T> &dc, cudaStream_t st, cudaEvent_t *ev)
     mark(1);
     if (F > 0) {
         k_face_pre<T, D, NC><<<cdiv(F, 128), 128, 0, st>>>(dc);
-        k_face_sum1<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
+        if (dc.sep1) {
+            const size_t sm = (size_t)SUM1_SEP_WARPS * 6 * (dc.cart_n[D - 1] + 1) * sizeof(T);
+            if (sm > 48 * 1024)
+                cudaFuncSetAttribute(k_face_sum1_sep<T, D, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_face_sum1_sep<T, D, NC><<<cdiv(F, SUM1_SEP_WARPS), 32 * SUM1_SEP_WARPS, sm, st>>>(dc);
+        } else {
+            k_face_sum1<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
+        }
         k_face_fin1<T, D, NC><<<cdiv(F, 128), 128, 0, st>>>(dc);
         if (dc.sep) k_face_sum2_sep<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
         else k_face_sum2<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);

@@ -107,6 +107,32 @@ def test_3d_box_moving_wall():
     _compare(o, g, what="3d box")
 
 
+def test_half_range_ties_on_axis_aligned_faces():
+    """Odd velocity counts put a line of nodes on u.n = 0 at every face of a quad
+    mesh: the half-range sums (direct and separable alike) give them half weight
+    on both sides (Sec. 2.4) and their flux vanishes."""
+    case = cs.cavity_case(n=8, nv=13, Kn=0.3, lid=0.3)
+    o, g = _pair(case, perturb=0.1)
+    o.step(3)
+    g.step(3)
+    _compare(o, g, what="ties 2d")
+
+
+def test_descending_velocity_axis():
+    """A tensor grid whose last axis descends is still a tensor grid, but takes
+    the direct half-range sums (the separable ones search an ascending axis)."""
+    case = cs.cavity_case(n=6, nv=11, Kn=0.3, lid=0.3)
+    nx = ny = 11
+    u = case["vgrid"]["u"].reshape(ny, nx, 2)[::-1].reshape(-1, 2)
+    w = case["vgrid"]["w"].reshape(ny, nx)[::-1].reshape(-1)
+    case = dict(case, vgrid={"dim": 2, "u": np.ascontiguousarray(u), "w": np.ascontiguousarray(w),
+                             "cart_n": [nx, ny, 0]})
+    o, g = _pair(case, perturb=0.1)
+    o.step(2)
+    g.step(2)
+    _compare(o, g, what="descending axis")
+
+
 def test_3d_sphere_tetrahedra():
     case = cs.sphere_case(n_cells=3000, nv=8, vmax=8.0, mach=2.0)
     o, g = _pair(case, perturb=0.05)
