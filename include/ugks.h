@@ -122,6 +122,7 @@ typedef struct {
     size_t f_bytes;            /* bytes of one copy of f */
     int32_t n_patches, patch_cells, vtile;  /* gather tiling in use */
     int64_t kernel_launches_per_step;
+    int64_t n_wall_faces;               /* faces of type UGKS_FACE_WALL */
 } ugks_info_t;
 
 /* Create a case: validates and copies the inputs, orders cells for locality,
@@ -151,6 +152,17 @@ ugks_status ugks_residual(ugks_case *c, double *res);
 /* Copy the state to host buffers: f[C][ncomp][nv] (FP64, caller cell order) and
  * W[C][dim+2] (conserved variables); either may be NULL.  Synchronises. */
 ugks_status ugks_get_state(ugks_case *c, double *f, double *W);
+
+/* Surface quantities of the last step at every wall face (Sec. 2.5), in the
+ * caller's face order: face[i] is the face id; with F_w the macroscopic wall
+ * flux of Eq. macroscopicFlux over the step, F_mw its momentum part and n_w
+ * the face normal (out of the fluid cell, into the wall), p[i] = F_mw . n_w,
+ * sigma[i] = |F_mw - p[i] n_w| and q[i] = F_w4 (energy), each divided by dt
+ * (the time average over the step).  The arrays hold n_wall_faces entries
+ * (ugks_info); any may be NULL.  Zero before the first step.  Synchronises.
+ * Pressure, shear and heat flux coefficients follow by dividing by
+ * rho_inf U_inf^2 / 2 (p, sigma) and rho_inf U_inf^3 / 2 (q). */
+ugks_status ugks_wall_quantities(ugks_case *c, int64_t *face, double *p, double *sigma, double *q);
 
 /* The state of selected cells only: for i < n, f[i][ncomp][nv] (FP64) and
  * W[i][dim+2] of caller cell cells[i] (either output may be NULL; ids may

@@ -77,6 +77,7 @@ def lib():
         L.or_residual.argtypes = [ct.c_void_p, D_P]
         L.or_wall_rho.argtypes = [ct.c_void_p, D_P]
         L.or_face_macro_flux.argtypes = [ct.c_void_p, D_P]
+        L.or_wall_quantities.argtypes = [ct.c_void_p, D_P, D_P, D_P]
         L.or_time_integrals.argtypes = [ct.c_double, ct.c_double, D_P]
         L.or_maxwellian.argtypes = [ct.c_int32, ct.c_double, D_P, ct.c_double, ct.c_int64, D_P, D_P, D_P]
         L.or_shakhov.argtypes = [ct.c_int32, ct.c_double, ct.c_double, D_P, ct.c_double, D_P,
@@ -121,6 +122,7 @@ class OracleCase:
         arrs["face_type"] = _c(mesh["face_type"], np.int32)
         arrs["face_tag"] = _c(mesh["face_tag"], np.int32)
         self._keep.append(arrs)
+        self.n_wall = int(np.count_nonzero(arrs["face_type"] == 1))
         m = _Mesh(D, self.C, self.F, _p(arrs["cell_xc"]), _p(arrs["cell_vol"]),
                   _p(arrs["face_cells"], I64_P), _p(arrs["face_n"]), _p(arrs["face_S"]),
                   _p(arrs["face_xc"]), _p(arrs["face_type"], I32_P), _p(arrs["face_tag"], I32_P),
@@ -174,6 +176,13 @@ class OracleCase:
         r = np.empty(max(n_wall, 1))
         lib().or_wall_rho(self._h, _p(r))
         return r[:n_wall]
+
+    def wall_quantities(self):
+        """p_w, sigma_w, q_w of the last step at the wall faces (face order)."""
+        n = max(self.n_wall, 1)
+        p, sg, q = np.empty(n), np.empty(n), np.empty(n)
+        lib().or_wall_quantities(self._h, _p(p), _p(sg), _p(q))
+        return p[:self.n_wall], sg[:self.n_wall], q[:self.n_wall]
 
     def face_macro_flux(self):
         F = np.empty((self.F, self.D + 2))

@@ -561,7 +561,7 @@ or_case *or_create(const or_mesh *m, const or_vgrid *v, const or_params *p,
     c->qs = (double *)malloc(sizeof(double) * (F ? F : 1) * 5);
     c->grad_k = (double *)malloc(sizeof(double) * C * nc * D);
     c->Fk = (double *)malloc(sizeof(double) * (F ? F : 1) * nc);
-    c->Fm = (double *)malloc(sizeof(double) * (F ? F : 1) * M);
+    c->Fm = (double *)calloc((size_t)(F ? F : 1) * M, sizeof(double));
     c->ghost_k = (double *)malloc(sizeof(double) * (F ? F : 1) * nc);
     size_t nwk = (size_t)(c->n_wall ? c->n_wall : 1) * Nv * nc;
     c->fin = (double *)malloc(sizeof(double) * nwk);
@@ -1132,6 +1132,33 @@ void or_residual(const or_case *c, double *res)
 void or_wall_rho(const or_case *c, double *rho_w)
 {
     for (int64_t s = 0; s < c->n_wall; ++s) rho_w[s] = c->rho_w[s];
+}
+
+/* Surface quantities at every wall face, in face order (Sec. 2.5): with F_w
+ * the macroscopic wall flux of Eq. macroscopicFlux over the last step,
+ * F_mw its momentum part and n_w the face normal (out of the fluid cell,
+ * into the wall), p_w = F_mw . n_w, sigma_w = |F_mw - p_w n_w|, q_w = F_w4
+ * (the energy component).  READING: F_w is integrated over the step, so the
+ * surface quantities are taken as its time average F_w / dt.  Zero before
+ * the first step. */
+void or_wall_quantities(const or_case *c, double *p, double *sigma, double *q)
+{
+    const int D = c->D, M = D + 2;
+    for (int64_t s = 0; s < c->n_wall; ++s) {
+        const int64_t f = c->wall_face[s];
+        const double *Fm = c->Fm + f * M;
+        const double *n = c->face_n + f * D;
+        double pn = 0.0;
+        for (int d = 0; d < D; ++d) pn += Fm[1 + d] * n[d];
+        double t2 = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double t = Fm[1 + d] - pn * n[d];
+            t2 += t * t;
+        }
+        p[s] = pn / c->dt;
+        sigma[s] = sqrt(t2) / c->dt;
+        q[s] = Fm[D + 1] / c->dt;
+    }
 }
 
 void or_face_macro_flux(const or_case *c, double *F)

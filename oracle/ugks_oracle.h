@@ -72,6 +72,8 @@ void or_residual(const or_case *c, double *res);
 void or_wall_rho(const or_case *c, double *rho_w);
 /* macroscopic flux of every face in the last step, F[F][D+2] */
 void or_face_macro_flux(const or_case *c, double *F);
+/* p_w, sigma_w, q_w of the last step at every wall face (face order), Sec. 2.5 */
+void or_wall_quantities(const or_case *c, double *p, double *sigma, double *q);
 
 /* ---- building blocks, exported for the pin tests ---- */
 /* Eq. c1..c5 integrated over [0, dt]; tau may be +inf */

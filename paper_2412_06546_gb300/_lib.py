@@ -66,7 +66,7 @@ class Info(ct.Structure):
                 ("nv_pad", ct.c_int64), ("dt", ct.c_double), ("step", ct.c_int64),
                 ("device_bytes", ct.c_size_t), ("f_bytes", ct.c_size_t), ("n_patches", ct.c_int32),
                 ("patch_cells", ct.c_int32), ("vtile", ct.c_int32),
-                ("kernel_launches_per_step", ct.c_int64)]
+                ("kernel_launches_per_step", ct.c_int64), ("n_wall_faces", ct.c_int64)]
 
 
 class Result(ct.Structure):
@@ -93,6 +93,7 @@ EXPORTS = {
     "ugks_get_state": (ct.c_int, [ct.c_void_p, D_P, D_P]),
     "ugks_set_state": (ct.c_int, [ct.c_void_p, D_P, D_P]),
     "ugks_get_cells": (ct.c_int, [ct.c_void_p, I64_P, ct.c_int64, D_P, D_P]),
+    "ugks_wall_quantities": (ct.c_int, [ct.c_void_p, I64_P, D_P, D_P, D_P]),
     "ugks_info": (ct.c_int, [ct.c_void_p, ct.POINTER(Info)]),
     "ugks_profile_begin": (ct.c_int, [ct.c_void_p, ct.c_int32]),
     "ugks_profile_end": (ct.c_int, [ct.c_void_p, D_P, ct.c_int32, ct.POINTER(ct.c_int32)]),
@@ -261,6 +262,15 @@ class Case:
         W = np.empty((self.C, self.D + 2))
         check(load().ugks_get_state(self._h, _p(f), _p(W)))
         return f, W
+
+    def wall_quantities(self):
+        """Face ids and p_w, sigma_w, q_w of the last step at the wall faces
+        (time averages over the step, Sec. 2.5)."""
+        n = self.info()["n_wall_faces"]
+        face = np.empty(n, dtype=np.int64)
+        p, sg, q = np.empty(n), np.empty(n), np.empty(n)
+        check(load().ugks_wall_quantities(self._h, face.ctypes.data_as(I64_P), _p(p), _p(sg), _p(q)))
+        return face, p, sg, q
 
     def cells(self, ids, with_f=True):
         """f [n][ncomp][nv] and W [n][dim+2] of the caller cells ``ids``."""

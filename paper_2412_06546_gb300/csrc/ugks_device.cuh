@@ -104,6 +104,7 @@ struct DevCase {
     const int *ftag;
     double inf_W[MAXM];
     double *rho_w;                // [NW]
+    double *wall_F;               // [NW][D+2] macroscopic wall flux over the last step (Eq. macroscopicFlux)
     T *wrec;                      // [NW][GREC]
     // per-step work
     T *crec;                      // [C][CREC] stage-1 record (W^n, q^n)

@@ -62,6 +62,8 @@ struct ugks_case {
     int P = 0, vtile = 0, n_patches = 0, n_vt = 0;
     long long *perm_d = nullptr;   // caller cell i -> internal cell
     std::vector<long long> perm_h; // the same on the host
+    std::vector<long long> wall_face_h;   // face id of every wall slot
+    std::vector<double> wall_n_h;         // [NW][D] its normal
     double *res_d = nullptr;       // [M]
     int *flags_d = nullptr;
     int n_res_blocks = 0;
@@ -650,6 +652,12 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
         dc.inf_W[D + 1] = p->inf_rho * (0.5 * ke + 1.5 * p->inf_T);
     }
     dc.rho_w = (double *)c->dalloc((size_t)std::max(c->NW, 1) * sizeof(double));
+    dc.wall_F = (double *)c->dalloc((size_t)std::max(c->NW, 1) * M * sizeof(double));
+    cuda_ok(cudaMemsetAsync(dc.wall_F, 0, (size_t)std::max(c->NW, 1) * M * sizeof(double), c->stream), "memset");
+    c->wall_face_h.assign(h.wface.begin(), h.wface.end());
+    c->wall_n_h.resize((size_t)c->NW * D);
+    for (int s = 0; s < c->NW; ++s)
+        for (int d = 0; d < D; ++d) c->wall_n_h[(size_t)s * D + d] = m->face_n[(size_t)h.wface[s] * D + d];
     dc.wrec = (T *)c->dalloc((size_t)std::max(c->NW, 1) * ugks::GREC * sizeof(T));
     dc.crec = (T *)c->dalloc((size_t)c->C * ugks::CREC * sizeof(T));
     dc.krec = (T *)c->dalloc((size_t)c->C * ugks::CREC * sizeof(T));
@@ -1000,6 +1008,34 @@ ugks_status ugks_get_state(ugks_case *c, double *f, double *W)
     });
 }
 
+ugks_status ugks_wall_quantities(ugks_case *c, int64_t *face, double *p, double *sigma, double *q)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        const int D = c->D, M = D + 2, NW = c->NW;
+        if (NW == 0) return;
+        std::vector<double> F((size_t)NW * M);
+        const double *Fd = c->prec == UGKS_FP64 ? c->d64.wall_F : c->d32.wall_F;
+        cuda_ok(cudaMemcpyAsync(F.data(), Fd, F.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                "wall flux copy");
+        cuda_ok(cudaStreamSynchronize(c->stream), "sync");
+        for (int s = 0; s < NW; ++s) {
+            const double *Fs = &F[(size_t)s * M];
+            const double *n = &c->wall_n_h[(size_t)s * D];
+            double pn = 0.0, t2 = 0.0;
+            for (int d = 0; d < D; ++d) pn += Fs[1 + d] * n[d];
+            for (int d = 0; d < D; ++d) {
+                const double t = Fs[1 + d] - pn * n[d];
+                t2 += t * t;
+            }
+            if (face) face[s] = c->wall_face_h[s];
+            if (p) p[s] = pn / c->dt;
+            if (sigma) sigma[s] = std::sqrt(t2) / c->dt;
+            if (q) q[s] = Fs[D + 1] / c->dt;
+        }
+    });
+}
+
 ugks_status ugks_get_cells(ugks_case *c, const int64_t *cells, int64_t n, double *f, double *W)
 {
     return guard([&] {
@@ -1127,6 +1163,7 @@ ugks_status ugks_info(const ugks_case *c, ugks_info_t *info)
         info->patch_cells = c->P;
         info->vtile = c->vtile;
         info->kernel_launches_per_step = 5 + (c->F > 0 ? 5 : 0) + (c->NW > 0 ? 1 : 0);
+        info->n_wall_faces = c->NW;
     });
 }
 

@@ -878,7 +878,9 @@ __global__ void k_face_fin2(DevCase<T> dc)
 template <typename T, int D, int NC>
 __global__ void __launch_bounds__(256) k_wall_sum(DevCase<T> dc)
 {
-    __shared__ T red[2][8];
+    constexpr int M = D + 2;
+    constexpr int NR = 2 + 2 * M;               // num, den, outgoing moments A, incoming moments B
+    __shared__ T red[NR][8];
     const int s = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (s >= dc.NW) return;
@@ -899,12 +901,20 @@ __global__ void __launch_bounds__(256) k_wall_sum(DevCase<T> dc)
         n[d] = dc.fn[(size_t)f * D + d];
         r[d] = dc.frL[(size_t)f * D + d];
     }
+    const T dt = dc.dtT;
     const T hdt = T(0.5) * dc.dtT;
     const size_t rs = (size_t)NC * dc.nvp;
-    T num = 0, den = 0;
+    // num / den: zero net mass flux (Eq. maxWalldes); A / B: moments (Eq.
+    // macroscopicFlux) of the outgoing flux and of the incoming flux of the
+    // unit-density wall Maxwellian over the step, so that F_w = A + rho_w B
+    T v[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) v[i] = 0;
     for (int k = threadIdx.x; k < dc.nvp; k += blockDim.x) {
         T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
         T un = normal_velocity<T, D>(u, n);
+        T Fh = 0, Fb = 0;
+        int off = -1;
         if (un > T(0)) {
             T g[NC][D];
             cell_slope<T, D, NC>(dc, dc.f_cur, c, k, u, g);
@@ -913,29 +923,57 @@ __global__ void __launch_bounds__(256) k_wall_sum(DevCase<T> dc)
                 hin += g[0][d] * r[d];
                 ug += u[d] * g[0][d];
             }
-            num += dc.w[k] * un * (hin - hdt * ug);
+            v[0] += dc.w[k] * un * (hin - hdt * ug);
+            Fh = dt * un * (hin - hdt * ug);
+            if (NC == 2) {
+                T bin = dc.f_cur[(size_t)c * rs + (size_t)(NC - 1) * dc.nvp + k], ugb = 0;
+                for (int d = 0; d < D; ++d) {
+                    bin += g[NC - 1][d] * r[d];
+                    ugb += u[d] * g[NC - 1][d];
+                }
+                Fb = dt * un * (bin - hdt * ugb);
+            }
+            off = 2;
         } else if (un < T(0)) {
-            den += dc.w[k] * un * maxwell_h<T, D>(wr, u);
+            const T H = maxwell_h<T, D>(wr, u);
+            v[1] += dc.w[k] * un * H;
+            Fh = dt * un * H;
+            Fb = wr[GR_NB] * Fh;
+            off = 2 + M;
+        }
+        if (off >= 0) {
+            const T wk = dc.w[k];
+            T u2 = 0;
+            for (int d = 0; d < D; ++d) u2 += u[d] * u[d];
+            T mom[M];
+            mom[0] = wk * Fh;
+            for (int d = 0; d < D; ++d) mom[1 + d] = wk * u[d] * Fh;
+            mom[D + 1] = T(0.5) * wk * (u2 * Fh + (NC == 2 ? Fb : T(0)));
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                if (off == 2) v[2 + i] += mom[i];
+                else v[2 + M + i] += mom[i];
+            }
         }
     }
-    num = warp_sum(num);
-    den = warp_sum(den);
-    if (lane == 0) {
-        red[0][warp] = num;
-        red[1][warp] = den;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const T t = warp_sum(v[i]);
+        if (lane == 0) red[i][warp] = t;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            a += (double)red[0][w];
-            b += (double)red[1][w];
+        double a[NR];
+        for (int i = 0; i < NR; ++i) {
+            a[i] = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a[i] += (double)red[i][w];
         }
-        const double rw = -a / b;
+        const double rw = -a[0] / a[1];
         dc.rho_w[s] = rw;
         T *w = dc.wrec + (size_t)s * GREC;
         for (int i = 0; i < GREC; ++i) w[i] = wr[i];
         w[GR_PREF] = (T)pref_of(rw, lw, D);
+        for (int m = 0; m < M; ++m) dc.wall_F[(size_t)s * M + m] = a[2 + m] + rw * a[2 + M + m];
     }
 }
 

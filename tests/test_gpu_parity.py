@@ -133,6 +133,31 @@ def test_descending_velocity_axis():
     _compare(o, g, what="descending axis")
 
 
+@pytest.mark.parametrize("precision", [_lib.FP64, _lib.FP32])
+def test_wall_surface_quantities(precision):
+    """p_w, sigma_w and q_w (Sec. 2.5) of the step against the oracle: the
+    cavity with a moving lid, the Mach-3 cylinder and the sphere, two steps
+    from a perturbed state.  Shear and heat flux are small differences of the
+    one-sided fluxes, whose size is that of the pressure, so all three are
+    compared relative to the largest pressure (heat flux: or its own largest
+    value, if larger)."""
+    tol = 1e-12 if precision == _lib.FP64 else 1e-5
+    for case in (cs.cavity_case(n=10, nv=16, Kn=0.2, lid=0.3),
+                 cs.cylinder_case(n_cells=900, nvx=16, nvy=14, mach=3.0),
+                 cs.sphere_case(n_cells=1200, nv=8, vmax=7.0, mach=2.0)):
+        o, g = _pair(case, precision=precision, perturb=0.05)
+        o.step(2)
+        g.step(2)
+        face, p, sg, q = g.wall_quantities()
+        po, so, qo = o.wall_quantities()
+        assert np.array_equal(face, np.nonzero(np.asarray(case["mesh"]["face_type"]) == 1)[0])
+        ps = np.abs(po).max()
+        assert np.abs(p - po).max() <= tol * ps
+        assert np.abs(sg - so).max() <= tol * ps
+        assert np.abs(q - qo).max() <= tol * max(np.abs(qo).max(), ps)
+        g.close()
+
+
 def test_3d_sphere_tetrahedra():
     case = cs.sphere_case(n_cells=3000, nv=8, vmax=8.0, mach=2.0)
     o, g = _pair(case, perturb=0.05)

@@ -599,3 +599,46 @@ def test_impulsive_hypersonic_start_stays_physical():
         U = W[:, 1:3] / W[:, :1]
         T = (2 / 3) * (W[:, 3] / W[:, 0] - 0.5 * (U ** 2).sum(1))
         assert np.isfinite(W).all() and W[:, 0].min() > 0 and T.min() > 0
+
+
+# ---------------------------------------------------------------- wall surface quantities
+def _wall_box(vg, T_gas, walls, Kn=float("inf")):
+    """4x4 quads in the unit square, a uniform gas at rest (rho = 1, T_gas);
+    left, bottom and top walls carry tag 0, the right wall tag 1.  One step;
+    returns p_w, sigma_w, q_w and the tag of every wall face."""
+    mesh = cs.quad_mesh(4, 4, left=("wall", 0), right=("wall", 1), bottom=("wall", 0), top=("wall", 0))
+    pr = cs.params(Kn, walls=walls)
+    o = oracle.OracleCase(mesh, vg, pr, cs.uniform_state(16, 2, T=T_gas))
+    o.step(1)
+    p, sg, q = o.wall_quantities()
+    return p, sg, q, mesh["face_tag"][mesh["face_type"] == 1]
+
+
+def test_wall_quantities_of_a_rest_gas():
+    """Gas at rest between walls at its own temperature: the wall pressure is
+    p = rho T, with no shear and no heat flux (Sec. 2.5 definitions; the full
+    second moment of a Maxwellian on a symmetric grid)."""
+    vg = cs.cartesian_vgrid((40, 40), (-10, -10), (10, 10))     # tails cut at 8.8 sigma
+    T = 1.3
+    p, sg, q, _ = _wall_box(vg, T, [{"T": T, "U": [0, 0, 0]}, {"T": T, "U": [0, 0, 0]}])
+    assert len(p) == 16
+    assert np.abs(p - T).max() <= 1e-10
+    assert np.abs(sg).max() <= 1e-13 and np.abs(q).max() <= 1e-13
+
+
+def test_wall_quantities_free_molecular_closed_forms():
+    """First step at a diffuse wall from a uniform gas at rest (rho = 1, T):
+    with the particle flux G = rho sqrt(T / 2 pi) onto the wall, a wall at
+    T_w moving tangentially with U_t gives, in the continuum of velocities,
+    p_w = rho T / 2 + rho sqrt(T T_w) / 2, sigma_w = G |U_t| and the effusion
+    energy flux q_w = G (2 T - 2 T_w - U_t^2 / 2).  The half-range sums carry
+    an O(h^2) quadrature error at u_n = 0, so the normal axis is fine."""
+    vg = cs.cartesian_vgrid((401, 41), (-10, -8), (10, 8))
+    T, Tw, Ut = 1.0, 2.0, 0.5
+    p, sg, q, tag = _wall_box(vg, T, [{"T": T, "U": [0, 0, 0]}, {"T": Tw, "U": [0, Ut, 0]}])
+    G = np.sqrt(T / (2 * np.pi))
+    right = tag == 1
+    assert right.sum() == 4
+    np.testing.assert_allclose(p[right], 0.5 * T + 0.5 * np.sqrt(T * Tw), rtol=2e-3)
+    np.testing.assert_allclose(sg[right], G * Ut, rtol=2e-3)
+    np.testing.assert_allclose(q[right], G * (2 * T - 2 * Tw - 0.5 * Ut * Ut), rtol=2e-3)
