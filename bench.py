@@ -91,11 +91,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
 
 
-def _dist():
+def _dist(backend="nccl"):
+    """One process per GPU (torchrun): every rank runs its own replica of the
+    workload; the only collectives are the timing barriers and reductions."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
         return dist, dist.get_rank(), ws
     return None, 0, 1
 
@@ -139,10 +141,10 @@ def _time_steps(torch, g, steps, warmup, dist, sampler_index, profile=True):
     return ms, groups, cs.summary()
 
 
-def _max_over_ranks(torch, dist, v):
+def _max_over_ranks(torch, dist, v, device="cuda"):
     if not dist:
         return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -223,13 +225,30 @@ def _e2e(torch, g, args, dist, ws, C, Nv, info):
             "d2h_bytes_per_step": int(C * (2 * info["dim"] + 2) * 8)}
 
 
-def _serving(args, torch, lib):
+def _shard(items, rank, ws):
+    """The requests a rank serves: independent cases go to independent GPUs."""
+    return list(items)[rank::ws]
+
+
+def _combine_serving(dist, lat, span, cvu, conv):
+    """Merge the ranks' serving results: all latencies, the longest makespan,
+    the summed cell-velocity updates and converged counts."""
+    if not dist:
+        return list(lat), span, cvu, conv
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, (list(map(float, lat)), float(span), int(cvu), int(conv)))
+    return ([x for p in parts for x in p[0]], max(p[1] for p in parts), sum(p[2] for p in parts),
+            sum(p[3] for p in parts))
+
+
+def _serving(args, torch, lib, dist=None, rank=0, ws=1):
     """Serving leg: closed run (all requests at t = 0) to calibrate capacity,
     then Poisson arrivals at 1.5x that capacity; p50 / p99 of the time from
-    arrival to completion and the aggregate cell-velocity rate."""
+    arrival to completion and the aggregate cell-velocity rate.  With several
+    ranks each serves its share of the stream on its own GPU."""
     import numpy as np
     from paper_2412_06546_gb300 import serving
-    reqs = serving.request_stream(args.serve_n, seed=4)
+    reqs = _shard(serving.request_stream(args.serve_n, seed=4), rank, ws)
     budget = int(args.serve_budget_gb * (1 << 30))
 
     def run(arrivals):
@@ -240,21 +259,25 @@ def _serving(args, torch, lib):
         st = srv.stats()
         res = [srv.poll(t) for t in tickets]
         srv.close()
-        lat = np.array([r["t_done"] - r["t_arrive"] for r in res])
+        lat = [r["t_done"] - r["t_arrive"] for r in res]
         span = max(r["t_done"] for r in res) - t0
         conv = sum(1 for r in res if r["state"] == lib.REQ_DONE and r["status"] == 0)
-        return ok, lat, span, st["total_cvu"], conv, res
+        return ok, lat, span, st["total_cvu"], conv
 
-    ok0, lat0, span0, cvu0, conv0, _ = run(np.zeros(len(reqs)))
+    ok0, lat0, span0, cvu0, conv0 = run(np.zeros(len(reqs)))
     rate = 1.5 * len(reqs) / span0                 # offered load 1.5x the closed-run capacity
-    arr = serving.poisson_arrivals(len(reqs), rate, seed=44)
-    ok1, lat1, span1, cvu1, conv1, res1 = run(arr)
-    return {"requests": len(reqs), "tol": args.serve_tol, "max_steps": args.serve_max_steps,
+    arr = serving.poisson_arrivals(len(reqs), rate, seed=44 + rank)
+    ok1, lat1, span1, cvu1, conv1 = run(arr)
+    lat0, span0, cvu0, conv0 = _combine_serving(dist, lat0, span0, cvu0, conv0)
+    lat1, span1, cvu1, conv1 = _combine_serving(dist, lat1, span1, cvu1, conv1)
+    return {"requests": args.serve_n, "tol": args.serve_tol, "max_steps": args.serve_max_steps,
             "steps_per_tick": args.serve_tick, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
-            "arrival_rate_per_s": rate, "p50_s": float(np.percentile(lat1, 50)), "p99_s": float(np.percentile(lat1, 99)),
-            "aggregate_cvu_per_s": cvu1 / span1, "converged": conv1, "finished": bool(ok1),
-            "closed_run": {"makespan_s": span0, "aggregate_cvu_per_s": cvu0 / span0, "p50_s": float(np.percentile(lat0, 50)),
-                           "p99_s": float(np.percentile(lat0, 99)), "converged": conv0},
+            "arrival_rate_per_s": rate * ws, "p50_s": float(np.percentile(lat1, 50)),
+            "p99_s": float(np.percentile(lat1, 99)), "aggregate_cvu_per_s": cvu1 / span1, "converged": conv1,
+            "finished": bool(ok1),
+            "closed_run": {"makespan_s": span0, "aggregate_cvu_per_s": cvu0 / span0,
+                           "p50_s": float(np.percentile(lat0, 50)), "p99_s": float(np.percentile(lat0, 99)),
+                           "converged": conv0},
             "workload": "seeded cavity/cylinder stream: cells 1k-4k, N^2 velocities N in [16, 32], "
                         "Kn log-uniform [1e-3, 10], Mach [0.1, 6], FP32 storage"}
 
@@ -371,7 +394,7 @@ def main():
 
     serving_res = None
     if not args.no_serving:
-        serving_res = _serving(args, torch, _lib)
+        serving_res = _serving(args, torch, _lib, dist, rank, ws)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -117,6 +117,7 @@ struct DevCase {
     double *fUref;                // [F][D]
     double *fsum1, *fsum2;        // [F][S1], [F][S2]
     double *fprim0;               // [F][D+2] rho0, U0, lam0
+    double *fqs;                  // [F][5] time integrals q1..q5 of the interface
     double *dW_part;              // [C][n_vt][D+2]
     double *res_part;             // [n_res_blocks][2(D+2)]
     int *flags;                   // [1] numeric failure flag

@@ -672,6 +672,7 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     const int NS = M * (M + 1) / 2;
     dc.fsum2 = (double *)c->dalloc(Fm * NS * (D + 1) * sizeof(double));
     dc.fprim0 = (double *)c->dalloc(Fm * M * sizeof(double));
+    dc.fqs = (double *)c->dalloc(Fm * 5 * sizeof(double));
     // sized for the smallest velocity tile, so that the autotuner may retile
     dc.dW_part = (double *)c->dalloc((size_t)c->C * (c->nvp / 32) * M * sizeof(double));
     dc.res_part = (double *)c->dalloc((size_t)c->n_res_blocks * 2 * M * sizeof(double));

@@ -547,7 +547,7 @@ __global__ void k_face_fin1(DevCase<T> dc)
     r[FR_PREF] = (T)pref_of(p.rho, p.lam, D);
     const double kappa = 4.0 * (1.0 - dc.Pr) * p.lam * p.lam / (5.0 * p.rho);
     for (int d = 0; d < 3; ++d) r[FR_KQ + d] = d < D ? (T)(kappa * dc.fq0[(size_t)f * D + d]) : T(0);
-    double qs[5];
+    double *qs = dc.fqs + (size_t)f * 5;         // kept in FP64 for k_face_fin2
     time_integrals(dc.dt, tau_of(dc, p.rho, p.T), qs);
     for (int i = 0; i < 5; ++i) r[FR_QS + i] = (T)qs[i];
     r[FR_NB] = (T)(dc.nxi / (2.0 * p.lam));
@@ -822,8 +822,7 @@ __global__ void k_face_fin2(DevCase<T> dc)
     const double kappa = 4.0 * (1.0 - dc.Pr) * lam0 * lam0 / (5.0 * rho0);
     double kq[D];
     for (int d = 0; d < D; ++d) kq[d] = kappa * dc.fq0[(size_t)f * D + d];
-    double qs[5];
-    time_integrals(dc.dt, tau_of(dc, rho0, 1.0 / (2.0 * lam0)), qs);
+    const double *qs = dc.fqs + (size_t)f * 5;   // time integrals of k_face_fin1
     T *x = dc.xrec + (size_t)f * XREC;
     for (int d = 0; d < 3; ++d) x[XR_U + d] = d < D ? (T)U0[d] : T(0);
     x[XR_PREF] = (T)pref_of(rho0, lam0, D);
