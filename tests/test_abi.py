@@ -6,6 +6,8 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
+
 import pytest
 
 from paper_2412_06546_gb300 import _lib, build
@@ -60,19 +62,64 @@ int main(void) {
                          _lib.Params.vtile.offset, _lib.Info.kernel_launches_per_step.offset]
 
 
-def test_errors_are_reported_without_a_gpu(lib):
+def _bad_inputs():
+    from paper_2412_06546_gb300 import cases
+    base = cases.cavity_case(n=3, nv=4)
+
+    def with_mesh(**kw):
+        m = {k: (v.copy() if hasattr(v, "copy") else v) for k, v in base["mesh"].items()}
+        for k, f in kw.items():
+            f(m)
+        return m, base["vgrid"], base["params"]
+
+    def neg_vol(m):
+        m["cell_vol"][1] = -1.0
+
+    def bad_owner(m):
+        m["face_cells"][0, 0] = 99
+
+    def bad_neighbour(m):
+        i = int(np.nonzero(np.asarray(m["face_type"]) == 0)[0][0])
+        m["face_cells"][i, 1] = -5
+
+    def bad_tag(m):
+        i = int(np.nonzero(np.asarray(m["face_type"]) == 1)[0][0])
+        m["face_tag"][i] = 7
+
+    vg_empty = {"dim": 2, "u": np.zeros((0, 2)), "w": np.zeros(0), "cart_n": [0, 0, 0]}
+    return {
+        "volume": with_mesh(v=neg_vol),
+        "owner out of range": with_mesh(o=bad_owner),
+        "neighbour out of range": with_mesh(n=bad_neighbour),
+        "wall tag": with_mesh(t=bad_tag),
+        "velocity count": (base["mesh"], vg_empty, base["params"]),
+        "cfl > 0 or dt > 0": (base["mesh"], base["vgrid"], dict(base["params"], cfl=0.0, dt=0.0)),
+        "Kn > 0": (base["mesh"], base["vgrid"], dict(base["params"], Kn=-1.0)),
+    }
+
+
+@pytest.mark.parametrize("what", list(_bad_inputs().keys()))
+def test_errors_are_reported_without_a_gpu(lib, what):
     """Invalid input is rejected with UGKS_EINVAL and a message before any
     device call."""
     from paper_2412_06546_gb300 import cases
-    case = cases.cavity_case(n=3, nv=4)
-    mesh = dict(case["mesh"])
-    mesh["cell_vol"] = mesh["cell_vol"].copy()
-    mesh["cell_vol"][1] = -1.0
-    (m, v, p), keep = _lib.make_structs(mesh, case["vgrid"], case["params"], case["init"])
+    mesh, vg, pr = _bad_inputs()[what]
+    init = cases.uniform_state(len(mesh["cell_vol"]), 2)
+    (m, v, p), keep = _lib.make_structs(mesh, vg, pr, init)
     h = ct.c_void_p()
     code = lib.ugks_create(ct.byref(m), ct.byref(v), ct.byref(p), None, None, ct.byref(h))
-    assert code == 1 and b"volume" in lib.ugks_last_error()
+    assert code == 1 and what.encode() in lib.ugks_last_error(), lib.ugks_last_error()
     assert not h.value
+
+
+def test_empty_mesh_is_rejected(lib):
+    from paper_2412_06546_gb300 import cases
+    case = cases.cavity_case(n=3, nv=4)
+    (m, v, p), keep = _lib.make_structs(case["mesh"], case["vgrid"], case["params"], case["init"])
+    m.n_cells = 0
+    h = ct.c_void_p()
+    assert lib.ugks_create(ct.byref(m), ct.byref(v), ct.byref(p), None, None, ct.byref(h)) == 1
+    assert b"n_cells > 0" in lib.ugks_last_error() and not h.value
 
 
 def test_no_cpu_fallback_without_library(tmp_path):

@@ -158,6 +158,61 @@ def test_wall_surface_quantities(precision):
         g.close()
 
 
+def test_near_continuum_stiff_collision():
+    """Kn = 1e-4: dt / tau is far above 1, so the time integrals take their
+    closed forms and stage 2 is stiff."""
+    case = cs.cavity_case(n=8, nv=12, Kn=1e-4, lid=0.3)
+    o, g = _pair(case, perturb=0.1)
+    o.step(3)
+    g.step(3)
+    _compare(o, g, what="near continuum")
+
+
+def test_single_cell_between_walls():
+    """One cell, four walls: no least-squares neighbours (zero slopes), a patch
+    of one cell with an empty ring, walls of two temperatures."""
+    mesh = cs.quad_mesh(1, 1, left=("wall", 0), right=("wall", 1), bottom=("wall", 0), top=("wall", 0))
+    case = {"mesh": mesh, "vgrid": cs.cartesian_vgrid((12, 12), (-5, -5), (5, 5)),
+            "params": cs.params(0.5, walls=[{"T": 1.0, "U": [0, 0, 0]}, {"T": 1.5, "U": [0, 0.2, 0]}]),
+            "init": cs.uniform_state(1, 2)}
+    o, g = _pair(case, perturb=0.1)
+    o.step(4)
+    g.step(4)
+    _compare(o, g, what="single cell")
+
+
+def test_velocity_set_smaller_than_a_tile():
+    """25 velocities in a tile of 64: 39 padding velocities (u = 0, w = 0)."""
+    case = cs.cylinder_case(n_cells=700, nvx=5, nvy=5, mach=0.5, vx=(-5, 5), vy=(-5, 5))
+    o, g = _pair(case, perturb=0.05, vtile=64)
+    o.step(2)
+    g.step(2)
+    _compare(o, g, what="25 velocities")
+
+
+def test_explicit_time_step():
+    """A caller-given dt replaces the CFL step on both sides."""
+    case = cs.cylinder_case(n_cells=900, nvx=14, nvy=12, mach=2.0)
+    pr = dict(case["params"], dt=1e-3)
+    o, g = _pair(case, params=pr, perturb=0.05)
+    assert g.info()["dt"] == 1e-3 == o.dt
+    o.step(2)
+    g.step(2)
+    _compare(o, g, what="explicit dt")
+
+
+def test_fp32_storage_form_sphere_100_steps():
+    """The FP32-storage form in 3D (one stored component), 100 steps: W within
+    1e-5 (relative L2) of the FP64 oracle."""
+    case = cs.sphere_case(n_cells=1200, nv=8, vmax=7.0, mach=2.0)
+    o, g = _pair(case, precision=_lib.FP32, perturb=0.05)
+    o.step(100)
+    g.step(100)
+    _, Wo, _ = o.state()
+    _, Wg = g.state(with_f=False)
+    assert _rel_l2(Wg, Wo) <= 1e-5
+
+
 def test_3d_sphere_tetrahedra():
     case = cs.sphere_case(n_cells=3000, nv=8, vmax=8.0, mach=2.0)
     o, g = _pair(case, perturb=0.05)
