@@ -213,6 +213,62 @@ def test_fp32_storage_form_sphere_100_steps():
     assert _rel_l2(Wg, Wo) <= 1e-5
 
 
+def _merge_pairs(mesh, frac, seed):
+    """A mixed mesh: a seeded share of interior faces is removed and the two
+    triangles on either side merged into one quadrilateral (volume-weighted
+    centroid), so cells have 3 or 4 faces."""
+    rng = np.random.default_rng(seed)
+    fc = np.asarray(mesh["face_cells"]).copy()
+    ft = np.asarray(mesh["face_type"])
+    C = len(mesh["cell_vol"])
+    taken = np.zeros(C, bool)
+    drop = []
+    for f in rng.permutation(np.nonzero(ft == 0)[0]):
+        a, b = fc[f]
+        if not taken[a] and not taken[b] and len(drop) < frac * C / 2:
+            taken[a] = taken[b] = True
+            drop.append(f)
+    into = np.arange(C)
+    vol = np.asarray(mesh["cell_vol"]).copy()
+    xc = np.asarray(mesh["cell_xc"]).copy()
+    for f in drop:
+        a, b = fc[f]
+        xc[a] = (vol[a] * xc[a] + vol[b] * xc[b]) / (vol[a] + vol[b])
+        vol[a] += vol[b]
+        into[b] = a
+    keep_cells = np.nonzero(into == np.arange(C))[0]
+    new_id = -np.ones(C, np.int64)
+    new_id[keep_cells] = np.arange(len(keep_cells))
+    keep_f = np.ones(len(ft), bool)
+    keep_f[drop] = False
+    nfc = fc[keep_f]
+    nfc = np.stack([new_id[into[nfc[:, 0]]], np.where(nfc[:, 1] >= 0, new_id[into[np.maximum(nfc[:, 1], 0)]], -1)], 1)
+    out = dict(mesh, cell_xc=xc[keep_cells], cell_vol=vol[keep_cells], face_cells=nfc)
+    for k in ("face_n", "face_S", "face_xc", "face_type", "face_tag", "face_shift"):
+        out[k] = np.ascontiguousarray(np.asarray(mesh[k])[keep_f])
+    return out
+
+
+def test_mixed_triangles_and_quadrilaterals():
+    """Cells with 3 and 4 faces in one mesh (face counts vary within a patch
+    and its ring)."""
+    case = cs.cylinder_case(n_cells=900, nvx=14, nvy=12, mach=2.0)
+    mesh = _merge_pairs(case["mesh"], 0.4, 3)
+    nf = np.bincount(np.concatenate([mesh["face_cells"][:, 0], mesh["face_cells"][mesh["face_cells"][:, 1] >= 0, 1]]))
+    assert set(np.unique(nf)) == {3, 4}
+    case = dict(case, mesh=mesh, init=cs.blended_start(mesh, [cs.freestream_speed(2.0), 0.0]))
+    for precision, tol in ((_lib.FP64, TOL64), (_lib.FP32, None)):
+        o, g = _pair(case, precision=precision, perturb=0.05)
+        o.step(2)
+        g.step(2)
+        if tol:
+            _compare(o, g, what="mixed mesh")
+        else:
+            _, Wo, _ = o.state()
+            _, Wg = g.state(with_f=False)
+            assert _rel_l2(Wg, Wo) <= 1e-5
+
+
 def test_3d_sphere_tetrahedra():
     case = cs.sphere_case(n_cells=3000, nv=8, vmax=8.0, mach=2.0)
     o, g = _pair(case, perturb=0.05)
