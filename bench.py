@@ -332,6 +332,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--patch", type=int, default=0)
     ap.add_argument("--vtile", type=int, default=0)
+    ap.add_argument("--w0-analytic", action="store_true",
+                    help="interface W0 from the analytic half-range moments (the variant of the N4 row)")
     args = ap.parse_args()
     if args.impl == "reference":
         args.ref_steps = args.ref_steps or args.steps
@@ -351,6 +353,8 @@ def main():
     from paper_2412_06546_gb300 import build, _lib
     build.build()
     case = _workload(args.workload)
+    if args.w0_analytic:
+        case = dict(case, params=dict(case["params"], w0_analytic=1))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32,
@@ -407,6 +411,7 @@ def main():
         "config": {"workload": args.workload, "cells": C, "nv": Nv, "faces": info["n_faces"],
                    "form": "fp32 storage, fp64 moments", "patch_cells": info["patch_cells"],
                    "vtile": info["vtile"], "l2": f"inputs larger than L2 (f {info['f_bytes'] / 1e9:.2f} GB per copy)",
+                   "w0": "analytic half-range moments" if args.w0_analytic else "discrete half-range sums",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "kernel": "k_gather", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None,

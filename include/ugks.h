@@ -101,6 +101,10 @@ typedef struct {
     int32_t patch_cells;    /* gather tiling: cells per patch (0: autotuned by timing the gather
                                kernel on this case, cached per case shape) */
     int32_t vtile;          /* gather tiling: velocities per tile, 32, 64 or 128 (0: automatic) */
+    int32_t w0_analytic;    /* interface equilibrium W0 (Sec. 2.4) from: 0 the discrete half-range
+                               sums over the velocity set (default), 1 the analytic half-range
+                               moments of the face-state Maxwellians over the continuous velocity
+                               space (erfc); the slopes of g0 use the discrete moments either way */
 } ugks_params;
 
 /* Device allocator.  alloc returns a device pointer of at least `bytes`

@@ -56,7 +56,8 @@ class _Params(ct.Structure):
                 ("omega", ct.c_double), ("cfl", ct.c_double), ("dt", ct.c_double),
                 ("limiter", ct.c_int32), ("venkat_K", ct.c_double), ("n_walls", ct.c_int32),
                 ("wall_T", D_P), ("wall_U", D_P), ("inf_rho", ct.c_double),
-                ("inf_U", ct.c_double * 3), ("inf_T", ct.c_double), ("n_threads", ct.c_int32)]
+                ("inf_U", ct.c_double * 3), ("inf_T", ct.c_double), ("n_threads", ct.c_int32),
+                ("w0_analytic", ct.c_int32)]
 
 
 def lib():
@@ -87,6 +88,8 @@ def lib():
         L.or_venkat.argtypes = [ct.c_double, ct.c_double, ct.c_double]
         L.or_face_equilibrium.argtypes = [ct.c_int32, ct.c_int64, D_P, D_P, D_P, D_P, D_P, D_P,
                                           D_P, D_P, D_P]
+        L.or_face_equilibrium_ex.argtypes = [ct.c_int32, ct.c_int64, D_P, D_P, D_P, D_P, D_P, D_P,
+                                             D_P, D_P, D_P, ct.c_int]
         L.or_moment_matrix.argtypes = [ct.c_int32, ct.c_int64, D_P, D_P, D_P, D_P]
         L.or_scalar_gradient.argtypes = [ct.c_void_p, D_P, D_P, ct.c_int32, D_P]
         L.or_micro_gradient.argtypes = [ct.c_void_p, D_P, D_P, D_P, D_P]
@@ -140,7 +143,7 @@ class OracleCase:
         p = _Params(params["Kn"], params.get("L_ref", 1.0), params["Pr"], params["omega"],
                     params["cfl"], params.get("dt", 0.0), params.get("limiter", 1),
                     params.get("venkat_K", 1.0), len(walls), _p(wT), _p(wU), inf["rho"],
-                    (ct.c_double * 3)(*iU), inf["T"], n_threads)
+                    (ct.c_double * 3)(*iU), inf["T"], n_threads, int(params.get("w0_analytic", 0)))
         init_a = _c(init) if init is not None else None
         self._h = L.or_create(ct.byref(m), ct.byref(v), ct.byref(p), _p(init_a))
         self.nc = L.or_ncomp(self._h)
@@ -240,12 +243,15 @@ def venkat(d1, d2, eps2):
     return lib().or_venkat(float(d1), float(d2), float(eps2))
 
 
-def face_equilibrium(D, u, w, n, WL, WR, gradW0):
+def face_equilibrium(D, u, w, n, WL, WR, gradW0, analytic=False):
+    """W0, spatial slopes a and time slope A of the interface equilibrium;
+    ``analytic``: W0 from the analytic half-range moments."""
     u, w, n, WL, WR, g = _c(u), _c(w), _c(n), _c(WL), _c(WR), _c(gradW0)
     W0 = np.empty(D + 2)
     a = np.empty((D, D + 2))
     A = np.empty(D + 2)
-    lib().or_face_equilibrium(D, len(w), _p(u), _p(w), _p(n), _p(WL), _p(WR), _p(g), _p(W0), _p(a), _p(A))
+    lib().or_face_equilibrium_ex(D, len(w), _p(u), _p(w), _p(n), _p(WL), _p(WR), _p(g), _p(W0), _p(a), _p(A),
+                                 1 if analytic else 0)
     return W0, a, A
 
 

@@ -297,16 +297,56 @@ void or_moment_matrix(int32_t D, int64_t nv, const double *u, const double *w, c
  * (H(0) = 1/2).  The spatial slope a^(d) solves M0 a^(d) = dW0/dx_d, and the
  * time slope A follows from the compatibility condition
  * int psi (u.a + A) g0 = 0, i.e. M0 A = -sum_d sum_k w_k u_d (a^(d).psi) psi g0. */
+/* Half-range moments of the Maxwellian (rho, U, lam), over u.n > 0 (sigma =
+ * +1) or u.n < 0 (sigma = -1), added into W0.  The velocity splits into u_n
+ * along the unit normal n and a tangential part; with U_n = U.n the normal
+ * moments over the half line are
+ *   <1>     = erfc(-sigma sqrt(lam) U_n) / 2,
+ *   <u_n>   = U_n <1> + e,   e = sigma exp(-lam U_n^2) / (2 sqrt(pi lam)),
+ *   <u_n^2> = (U_n^2 + 1/(2 lam)) <1> + U_n e,
+ * while the D-1 tangential components (mean U - U_n n) and the 3-D internal
+ * ones take full Gaussian moments (variance 1/(2 lam) each). */
+static void half_range_moments(int D, double rho, const double *U, double lam, const double *n, double sigma,
+                               double *W0)
+{
+    double Un = 0.0;
+    for (int d = 0; d < D; ++d) Un += U[d] * n[d];
+    const double m0 = 0.5 * erfc(-sigma * sqrt(lam) * Un);
+    const double e = sigma * exp(-lam * Un * Un) / (2.0 * sqrt(M_PI * lam));
+    const double m1 = Un * m0 + e;
+    const double m2 = (Un * Un + 0.5 / lam) * m0 + Un * e;
+    double Ut2 = 0.0;
+    W0[0] += rho * m0;
+    for (int d = 0; d < D; ++d) {
+        const double Ut = U[d] - Un * n[d];
+        Ut2 += Ut * Ut;
+        W0[1 + d] += rho * (m1 * n[d] + Ut * m0);
+    }
+    /* (D - 1) tangential + (3 - D) internal components: 2 of variance 1/(2 lam) */
+    W0[D + 1] += 0.5 * rho * (m2 + (Ut2 + 2.0 * 0.5 / lam) * m0);
+}
+
 void or_face_equilibrium(int32_t D, int64_t nv, const double *u, const double *w, const double *n,
                          const double *WL, const double *WR, const double *gradW0, double *W0,
                          double *a, double *A)
+{
+    or_face_equilibrium_ex(D, nv, u, w, n, WL, WR, gradW0, W0, a, A, 0);
+}
+
+void or_face_equilibrium_ex(int32_t D, int64_t nv, const double *u, const double *w, const double *n,
+                            const double *WL, const double *WR, const double *gradW0, double *W0,
+                            double *a, double *A, int analytic)
 {
     int M = D + 2;
     double rL, UL[MAXD], lL, rR, UR[MAXD], lR;
     prim_of(D, WL, &rL, UL, &lL);
     prim_of(D, WR, &rR, UR, &lR);
     for (int m = 0; m < M; ++m) W0[m] = 0.0;
-    for (int64_t k = 0; k < nv; ++k) {
+    if (analytic) {
+        half_range_moments(D, rL, UL, lL, n, +1.0, W0);
+        half_range_moments(D, rR, UR, lR, n, -1.0, W0);
+    }
+    for (int64_t k = 0; k < (analytic ? 0 : nv); ++k) {
         const double *uk = u + k * D;
         double un = 0.0, u2 = 0.0;
         for (int d = 0; d < D; ++d) {
@@ -856,8 +896,8 @@ static void one_step(or_case *c)
             /* Sec. 3.2: interface heat flux = average of the two cells */
             for (int d = 0; d < D; ++d) c->q0[f * D + d] = 0.5 * (c->q[i * D + d] + c->q[j * D + d]);
         }
-        or_face_equilibrium(D, Nv, c->u, c->w, c->face_n + f * D, WL, WR, g0, c->W0 + f * M,
-                            c->fa + f * D * M, c->fA + f * M);
+        or_face_equilibrium_ex(D, Nv, c->u, c->w, c->face_n + f * D, WL, WR, g0, c->W0 + f * M,
+                               c->fa + f * D * M, c->fA + f * M, c->p.w0_analytic);
         double rho0, U0[MAXD], lam0;
         prim_of(D, c->W0 + f * M, &rho0, U0, &lam0);
         or_time_integrals(dt, tau_of(c, rho0, lam0), c->qs + f * 5);

@@ -52,6 +52,8 @@ typedef struct {
     const double *wall_U;   /* [n_walls][3] */
     double inf_rho, inf_U[3], inf_T;
     int32_t n_threads;      /* OpenMP threads, <= 0: library default */
+    int32_t w0_analytic;    /* 1: W0 from the analytic half-range moments (continuous velocity
+                               space) instead of the discrete sums over the velocity set */
 } or_params;
 
 typedef struct or_case or_case;
@@ -94,6 +96,10 @@ double or_venkat(double d1, double d2, double eps2);
 void or_face_equilibrium(int32_t D, int64_t nv, const double *u, const double *w,
                          const double *n, const double *WL, const double *WR,
                          const double *gradW0, double *W0, double *a, double *A);
+/* the same, with W0 from the analytic half-range moments when analytic != 0 */
+void or_face_equilibrium_ex(int32_t D, int64_t nv, const double *u, const double *w, const double *n,
+                            const double *WL, const double *WR, const double *gradW0, double *W0,
+                            double *a, double *A, int analytic);
 /* moment matrix M0[(D+2)^2] of the Maxwellian of W0 on the discrete grid */
 void or_moment_matrix(int32_t D, int64_t nv, const double *u, const double *w,
                       const double *W0, double *M0);

@@ -49,7 +49,8 @@ class Params(ct.Structure):
                 ("limiter", ct.c_int32), ("venkat_K", ct.c_double), ("n_walls", ct.c_int32),
                 ("wall_T", D_P), ("wall_U", D_P), ("inf_rho", ct.c_double),
                 ("inf_U", ct.c_double * 3), ("inf_T", ct.c_double), ("precision", ct.c_int32),
-                ("prim_init", D_P), ("patch_cells", ct.c_int32), ("vtile", ct.c_int32)]
+                ("prim_init", D_P), ("patch_cells", ct.c_int32), ("vtile", ct.c_int32),
+                ("w0_analytic", ct.c_int32)]
 
 
 ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p)
@@ -172,7 +173,7 @@ def make_structs(mesh, vgrid, params, init=None, precision=FP64, patch_cells=0, 
     p = Params(params["Kn"], params.get("L_ref", 1.0), params["Pr"], params["omega"], params["cfl"],
                params.get("dt", 0.0), params.get("limiter", 1), params.get("venkat_K", 1.0), len(walls),
                _p(wT), _p(wU), inf["rho"], (ct.c_double * 3)(*iU), inf["T"], int(precision), _p(ini),
-               int(patch_cells), int(vtile))
+               int(patch_cells), int(vtile), int(params.get("w0_analytic", 0)))
     return (m, v, p), keep
 
 

@@ -61,6 +61,7 @@ struct DevCase {
     int nv, nvp;             // velocities, padded count
     double dt, Pr, omega, mu_ref, nxi;
     int limiter;
+    int w0_analytic;              // 1: W0 from the analytic half-range moments
     // velocity grid (padded), FP64 and T copies
     const double *ud[3], *wd;
     const T *u[3], *w;

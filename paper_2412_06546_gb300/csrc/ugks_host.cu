@@ -211,6 +211,7 @@ void validate(const ugks_mesh *m, const ugks_vgrid *v, const ugks_params *p)
     if (p->vtile != 0 && p->vtile != 32 && p->vtile != 64 && p->vtile != 128)
         fail(UGKS_EINVAL, "vtile must be 0, 32, 64 or 128");
     if (p->patch_cells < 0 || p->patch_cells > 4096) fail(UGKS_EINVAL, "patch_cells out of range");
+    if (p->w0_analytic != 0 && p->w0_analytic != 1) fail(UGKS_EINVAL, "w0_analytic must be 0 or 1");
 }
 
 // invert the DxD normal matrix by its adjugate
@@ -500,6 +501,7 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
                                   : 15.0 * std::sqrt(2.0 * M_PI) * p->Kn * p->L_ref /
                                         (2.0 * (5.0 - 2.0 * p->omega) * (7.0 - 2.0 * p->omega));
     dc.limiter = p->limiter ? 1 : 0;
+    dc.w0_analytic = p->w0_analytic ? 1 : 0;
     // velocities, padded with u = 0, w = 0
     for (int d = 0; d < 3; ++d) {
         dc.ud[d] = nullptr;

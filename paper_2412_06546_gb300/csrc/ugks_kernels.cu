@@ -306,6 +306,32 @@ __device__ __forceinline__ void side_record(const double *Ws, double nxi, T *rec
     rec[GR_NL2] = (T)(-p.lam * LOG2E);
 }
 
+// Analytic half-range moments of the Maxwellian p over u.n > 0 (sigma = +1)
+// or u.n < 0 (sigma = -1), added into the conserved components W.  Along the
+// unit normal, with U_n = U.n and e = sigma exp(-lam U_n^2) / (2 sqrt(pi lam)):
+// <1> = erfc(-sigma sqrt(lam) U_n) / 2, <u_n> = U_n <1> + e and
+// <u_n^2> = (U_n^2 + 1/(2 lam)) <1> + U_n e; the D-1 tangential components
+// (mean U - U_n n) and the 3-D internal ones are full Gaussians of variance
+// 1/(2 lam) each, two components in all.
+template <int D>
+__device__ void add_half_range(const Prim &p, const double n[D], double sigma, double *W)
+{
+    double Un = 0.0;
+    for (int d = 0; d < D; ++d) Un += p.U[d] * n[d];
+    const double m0 = 0.5 * erfc(-sigma * sqrt(p.lam) * Un);
+    const double e = sigma * exp(-p.lam * Un * Un) / (2.0 * sqrt(3.14159265358979323846 * p.lam));
+    const double m1 = Un * m0 + e;
+    const double m2 = (Un * Un + 0.5 / p.lam) * m0 + Un * e;
+    double Ut2 = 0.0;
+    W[0] += p.rho * m0;
+    for (int d = 0; d < D; ++d) {
+        const double Ut = p.U[d] - Un * n[d];
+        Ut2 += Ut * Ut;
+        W[1 + d] += p.rho * (m1 * n[d] + Ut * m0);
+    }
+    W[D + 1] += 0.5 * p.rho * (m2 + (Ut2 + 1.0 / p.lam) * m0);
+}
+
 template <typename T, int D, int NC>
 __global__ void k_face_pre(DevCase<T> dc)
 {
@@ -341,6 +367,25 @@ __global__ void k_face_pre(DevCase<T> dc)
     side_record<T, D>(WR, dc.nxi, dc.fside + (size_t)f * 2 * GREC + GREC);
     Prim pL = prim_of(WL, D), pR = prim_of(WR, D);
     for (int d = 0; d < D; ++d) dc.fUref[(size_t)f * D + d] = 0.5 * (pL.U[d] + pR.U[d]);
+    if (dc.w0_analytic) {
+        // W0 from the analytic half-range moments (continuous velocity space),
+        // stored centred at U_ref as the discrete sums of k_face_sum1 are
+        double n[D], W0[M];
+        for (int d = 0; d < D; ++d) n[d] = dc.fn_d[(size_t)f * D + d];
+        for (int m = 0; m < M; ++m) W0[m] = 0.0;
+        add_half_range<D>(pL, n, 1.0, W0);
+        add_half_range<D>(pR, n, -1.0, W0);
+        double *S = dc.fsum1 + (size_t)f * M;
+        double uS = 0.0, uu = 0.0;
+        S[0] = W0[0];
+        for (int d = 0; d < D; ++d) {
+            const double Ur = dc.fUref[(size_t)f * D + d];
+            S[1 + d] = W0[1 + d] - Ur * W0[0];
+            uS += Ur * W0[1 + d];
+            uu += Ur * Ur;
+        }
+        S[D + 1] = W0[D + 1] - uS + 0.5 * uu * W0[0];
+    }
 }
 
 // half-range moments: sum_k w psi_c [H(u_n) g_L + (1 - H(u_n)) g_R], centred at U_ref
@@ -1439,7 +1484,9 @@ static void pre_gather(const DevCase<T> &dc, cudaStream_t st, cudaEvent_t *ev)
     mark(1);
     if (F > 0) {
         k_face_pre<T, D, NC><<<cdiv(F, 128), 128, 0, st>>>(dc);
-        if (dc.sep1) {
+        if (dc.w0_analytic) {
+            // W0 came from k_face_pre
+        } else if (dc.sep1) {
             const size_t sm = (size_t)SUM1_SEP_WARPS * 6 * (dc.cart_n[D - 1] + 1) * sizeof(T);
             if (sm > 48 * 1024)
                 cudaFuncSetAttribute(k_face_sum1_sep<T, D, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

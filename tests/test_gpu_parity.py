@@ -269,6 +269,27 @@ def test_mixed_triangles_and_quadrilaterals():
             assert _rel_l2(Wg, Wo) <= 1e-5
 
 
+@pytest.mark.parametrize("precision", [_lib.FP64, _lib.FP32])
+def test_analytic_w0_variant(precision):
+    """The analytic-W0 variant (W0 from the erfc half-range moments of the
+    face-state Maxwellians) against the oracle run with the same option."""
+    for case in (cs.cavity_case(n=10, nv=16, Kn=0.2, lid=0.3),
+                 cs.cylinder_case(n_cells=1200, nvx=16, nvy=14, mach=3.0),
+                 cs.sphere_case(n_cells=1500, nv=8, vmax=7.0, mach=2.0)):
+        pr = dict(case["params"], w0_analytic=1)
+        o, g = _pair(case, precision=precision, params=pr, perturb=0.05)
+        steps = 2 if precision == _lib.FP64 else 100
+        o.step(steps)
+        g.step(steps)
+        if precision == _lib.FP64:
+            _compare(o, g, what="analytic W0")
+        else:
+            _, Wo, _ = o.state()
+            _, Wg = g.state(with_f=False)
+            assert _rel_l2(Wg, Wo) <= 1e-5
+        g.close()
+
+
 def test_3d_sphere_tetrahedra():
     case = cs.sphere_case(n_cells=3000, nv=8, vmax=8.0, mach=2.0)
     o, g = _pair(case, perturb=0.05)

@@ -642,3 +642,65 @@ def test_wall_quantities_free_molecular_closed_forms():
     np.testing.assert_allclose(p[right], 0.5 * T + 0.5 * np.sqrt(T * Tw), rtol=2e-3)
     np.testing.assert_allclose(sg[right], G * Ut, rtol=2e-3)
     np.testing.assert_allclose(q[right], G * (2 * T - 2 * Tw - 0.5 * Ut * Ut), rtol=2e-3)
+
+
+# ---------------------------------------------------------------- analytic W0 (the N4 variant)
+def test_analytic_w0_is_the_limit_of_the_discrete_sums():
+    """W0 from the analytic half-range moments equals the Richardson limit of
+    the discrete half-range sums (two independent routes), 2D and 3D."""
+    for D, n, WLp, WRp in ((2, [1.0, 0.0], (1.3, [0.4, 0.2], 1.2), (0.8, [-0.3, 0.1], 0.7)),
+                           (3, [0.0, 0.0, 1.0], (1.1, [0.2, -0.1, 0.5], 0.9), (0.7, [0.1, 0.3, -0.4], 1.4))):
+        WL = _conserved(D, WLp[0], np.array(WLp[1]), WLp[2])
+        WR = _conserved(D, WRp[0], np.array(WRp[1]), WRp[2])
+        vg0 = cs.cartesian_vgrid((5,) * D, (-1,) * D, (1,) * D)
+        ana, _, _ = oracle.face_equilibrium(D, vg0["u"], vg0["w"], np.array(n), WL, WR, np.zeros((D, D + 2)),
+                                            analytic=True)
+        est = []
+        for m in ((20, 40, 80) if D == 3 else (40, 80, 160)):
+            vg = cs.cartesian_vgrid((2 * m + 1,) * D, (-11,) * D, (11,) * D)
+            W0, _, _ = oracle.face_equilibrium(D, vg["u"], vg["w"], np.array(n), WL, WR, np.zeros((D, D + 2)))
+            est.append(W0)
+        r1 = (4 * est[1] - est[0]) / 3
+        r2 = (4 * est[2] - est[1]) / 3
+        rich = (16 * r2 - r1) / 15
+        assert np.abs(rich - ana).max() < (1e-8 if D == 2 else 1e-6), (D, rich, ana)
+
+
+def test_analytic_w0_special_cases():
+    """Equal face states give W0 = the state; when both face states move
+    along n far faster than their thermal speeds, all of W0 comes from the
+    upwind side (the downwind state has no particles with u.n < 0)."""
+    vg = cs.cartesian_vgrid((5, 5), (-1, -1), (1, 1))
+    n = np.array([0.6, 0.8])
+    W = _conserved(2, 1.2, np.array([0.3, -0.5]), 0.9)
+    W0, _, _ = oracle.face_equilibrium(2, vg["u"], vg["w"], n, W, W, np.zeros((2, 4)), analytic=True)
+    assert np.allclose(W0, W, rtol=1e-14, atol=1e-15)
+    WL = _conserved(2, 1.0, 12.0 * n, 1.0)       # sqrt(lam) U.n = 8.5: erfc(-8.5) / 2 = 1
+    WR = _conserved(2, 0.5, 15.0 * n, 2.0)       # sqrt(lam) U.n = 7.5: erfc(7.5) / 2 ~ 1e-26
+    W0, _, _ = oracle.face_equilibrium(2, vg["u"], vg["w"], n, WL, WR, np.zeros((2, 4)), analytic=True)
+    assert np.allclose(W0, WL, rtol=1e-12, atol=0)
+
+
+def test_analytic_w0_step_keeps_uniform_flow():
+    """Full steps with the analytic W0 leave a uniform flow unchanged on a
+    periodic mesh (as the discrete W0 does) and conserve mass, momentum and
+    energy from a non-uniform state."""
+    # a moving Maxwellian has no discrete heat flux only without the Shakhov
+    # term (BGK) or at rest (as in test_uniform_state_is_stationary)
+    for D, Pr, U in ((2, 1.0, [0.8, -0.5]), (2, 2.0 / 3.0, [0.0, 0.0]), (3, 1.0, [0.4, 0.3, -0.6])):
+        mesh, vg, pr = _periodic_case(D, Pr=Pr)
+        pr = dict(pr, w0_analytic=1)
+        C = len(mesh["cell_vol"])
+        o = oracle.OracleCase(mesh, vg, pr, cs.uniform_state(C, D, 1.2, U, 0.9))
+        f0, W0, _ = o.state()
+        o.step(3)
+        f1, W1, _ = o.state()
+        assert np.abs(f1 - f0).max() <= 1e-13 * np.abs(f0).max()
+        assert np.abs(W1 - W0).max() <= 1e-13 * np.abs(W0).max()
+        o2 = oracle.OracleCase(mesh, vg, pr, cs.smooth_state(mesh, 5, 0.1))
+        _, Wa, _ = o2.state()
+        o2.step(3)
+        _, Wb, _ = o2.state()
+        vol = mesh["cell_vol"]
+        tot = lambda W: (W * vol[:, None]).sum(axis=0)
+        assert np.abs(tot(Wb) - tot(Wa)).max() <= 2e-14 * np.abs(tot(Wa)).max()
