@@ -149,6 +149,18 @@ def _max_over_ranks(torch, dist, v, device="cuda"):
     return float(t.item())
 
 
+def _gather_sources():
+    """The gather pass's code: its section of ugks_kernels.cu (from the
+    "gather pass" to the "W update" marker) and all of ugks_device.cuh."""
+    csrc = os.path.join(ROOT, "paper_2412_06546_gb300", "csrc")
+    with open(os.path.join(csrc, "ugks_kernels.cu"), "rb") as fh:
+        k = fh.read()
+    a = k.index(b"// ------------------------------------------------------------ gather pass")
+    b = k.index(b"// ------------------------------------------------------------ W update")
+    with open(os.path.join(csrc, "ugks_device.cuh"), "rb") as fh:
+        return k[a:b] + fh.read()
+
+
 def _gather_traffic(workload, patch, vtile):
     """DRAM bytes of one gather launch from the committed ncu summary, while
     the gather's sources and tiling are those the counters were taken on
@@ -158,9 +170,7 @@ def _gather_traffic(workload, patch, vtile):
     if workload != WORKLOAD or not os.path.exists(prof):
         return None
     h = hashlib.sha256()
-    for f in ("ugks_kernels.cu", "ugks_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2412_06546_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    h.update(_gather_sources())
     fields = {}
     for line in open(prof):
         if ":" in line and line.split(":")[0] in ("gather-sources-sha256-16", "traffic-bytes-per-launch",
