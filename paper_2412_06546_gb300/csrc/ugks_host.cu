@@ -735,10 +735,13 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
     const int C = (int)c->C;
     auto smem_of = [&](const Host &hh, int vt) { return (size_t)hh.max_slope * c->NC * c->D * vt * esz; };
     if (best.first == 0) {
+        // tetrahedra have more faces and larger rings than triangles, and one
+        // stored component per velocity: smaller patches and wider velocity tiles
         const std::vector<int> pc = c->prec == UGKS_FP64 ? std::vector<int>{16, 24, 32, 48}
+                                    : c->D == 3          ? std::vector<int>{12, 16, 24, 32, 48}
                                                          : std::vector<int>{24, 32, 48, 64, 96};
         std::vector<int> vc = {c->vtile};
-        if (tune_vtile) vc = {32, 64};
+        if (tune_vtile) vc = c->D == 3 ? std::vector<int>{32, 64, 128} : std::vector<int>{32, 64};
         cuda_ok(ugks::launch_pre_gather(dc, c->stream), "autotune prep");
         cudaEvent_t e0, e1;
         cuda_ok(cudaEventCreate(&e0), "event");
@@ -841,10 +844,10 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         }
         const size_t esz = c->prec == UGKS_FP64 ? 8 : 4;
         // tiling: velocity tile of 32*TV, patch of P cells sized to shared memory
-        // velocity rows are padded to a multiple of 64 unless the tile is fixed,
-        // so that the autotuner may choose a tile of 32 or 64 velocities
+        // velocity rows are padded to a multiple of the widest tile the autotuner
+        // may choose (64 in 2D, 128 in 3D) unless the tile is fixed
         c->vtile = params->vtile > 0 ? params->vtile : kDefaultVtile(c->prec);
-        const int vpad = params->vtile > 0 ? params->vtile : 64;
+        const int vpad = params->vtile > 0 ? params->vtile : (c->D == 3 ? 128 : 64);
         int P = params->patch_cells > 0 ? params->patch_cells : (c->prec == UGKS_FP64 ? 32 : 48);
         Host h;
         int dev = 0;
