@@ -161,7 +161,7 @@ def _gather_sources():
         return k[a:b] + fh.read()
 
 
-def _gather_traffic(workload, patch, vtile):
+def _gather_traffic(workload, patch, vtile, threads):
     """DRAM bytes of one gather launch from the committed ncu summary, while
     the gather's sources and tiling are those the counters were taken on
     (else None: the kernel changed since)."""
@@ -179,7 +179,7 @@ def _gather_traffic(workload, patch, vtile):
             fields[k] = v.strip()
     if fields.get("gather-sources-sha256-16") != h.hexdigest()[:16]:
         return None
-    if fields.get("traffic-tiling") != f"patch {patch}, vtile {vtile}":
+    if fields.get("traffic-tiling") != f"patch {patch}, vtile {vtile}, threads {threads}":
         return None
     return int(fields["traffic-bytes-per-launch"])
 
@@ -342,6 +342,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--patch", type=int, default=0)
     ap.add_argument("--vtile", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0, help="gather CTA size, 256 or 512 (0: autotuned)")
     ap.add_argument("--w0-analytic", action="store_true",
                     help="interface W0 from the analytic half-range moments (the variant of the N4 row)")
     args = ap.parse_args()
@@ -368,7 +369,8 @@ def main():
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32,
-                      stream=stream.cuda_stream, patch_cells=args.patch, vtile=args.vtile)
+                      stream=stream.cuda_stream, patch_cells=args.patch, vtile=args.vtile,
+                      threads=args.threads)
     info = g.info()
     C, Nv, nc = info["n_cells"], info["nv"], info["ncomp"]
     ms, groups, clocks = _time_steps(torch, g, args.steps, args.warmup, dist, local)
@@ -420,12 +422,14 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "cells": C, "nv": Nv, "faces": info["n_faces"],
                    "form": "fp32 storage, fp64 moments", "patch_cells": info["patch_cells"],
-                   "vtile": info["vtile"], "l2": f"inputs larger than L2 (f {info['f_bytes'] / 1e9:.2f} GB per copy)",
+                   "vtile": info["vtile"], "gather_threads": info["gather_threads"],
+                   "l2": f"inputs larger than L2 (f {info['f_bytes'] / 1e9:.2f} GB per copy)",
                    "w0": "analytic half-range moments" if args.w0_analytic else "discrete half-range sums",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "kernel": "k_gather", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": _gather_traffic(args.workload, info["patch_cells"], info["vtile"]),
+                     "traffic": _gather_traffic(args.workload, info["patch_cells"], info["vtile"],
+                                                info["gather_threads"]),
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": g_ms, "group_share": share},
         "fp64_plain": {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": fp64_steps,

@@ -101,6 +101,8 @@ typedef struct {
     int32_t patch_cells;    /* gather tiling: cells per patch (0: autotuned by timing the gather
                                kernel on this case, cached per case shape) */
     int32_t vtile;          /* gather tiling: velocities per tile, 32, 64 or 128 (0: automatic) */
+    int32_t gather_threads; /* gather tiling: threads per CTA, 256 or 512 (512 only for UGKS_FP32 with
+                               vtile <= 64; 0: automatic, 256 unless the autotuner picks 512) */
     int32_t w0_analytic;    /* interface equilibrium W0 (Sec. 2.4) from: 0 the discrete half-range
                                sums over the velocity set (default), 1 the analytic half-range
                                moments of the face-state Maxwellians over the continuous velocity
@@ -127,6 +129,7 @@ typedef struct {
     int32_t n_patches, patch_cells, vtile;  /* gather tiling in use */
     int64_t kernel_launches_per_step;
     int64_t n_wall_faces;               /* faces of type UGKS_FACE_WALL */
+    int32_t gather_threads;             /* threads per CTA of the gather pass in use */
 } ugks_info_t;
 
 /* Create a case: validates and copies the inputs, orders cells for locality,

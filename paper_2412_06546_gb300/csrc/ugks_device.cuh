@@ -129,6 +129,7 @@ struct DevCase {
     const T *axis[3], *axw[3];
     // gather tiling
     int P, n_patches, n_vt, vtile;
+    int nth;                      // threads per gather CTA (256, or 512 for FP32 at TV <= 2)
     const int *ring_ptr, *ring_cells;
 };
 

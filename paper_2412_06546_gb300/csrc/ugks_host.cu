@@ -59,7 +59,7 @@ struct ugks_case {
     ugks::DevCase<double> d64{};
     ugks::DevCase<float> d32{};
     ugks::StepConfig cfg{};
-    int P = 0, vtile = 0, n_patches = 0, n_vt = 0;
+    int P = 0, vtile = 0, nth = 256, n_patches = 0, n_vt = 0;
     long long *perm_d = nullptr;   // caller cell i -> internal cell
     std::vector<long long> perm_h; // the same on the host
     std::vector<long long> wall_face_h;   // face id of every wall slot
@@ -212,6 +212,10 @@ void validate(const ugks_mesh *m, const ugks_vgrid *v, const ugks_params *p)
         fail(UGKS_EINVAL, "vtile must be 0, 32, 64 or 128");
     if (p->patch_cells < 0 || p->patch_cells > 4096) fail(UGKS_EINVAL, "patch_cells out of range");
     if (p->w0_analytic != 0 && p->w0_analytic != 1) fail(UGKS_EINVAL, "w0_analytic must be 0 or 1");
+    if (p->gather_threads != 0 && p->gather_threads != 256 && p->gather_threads != 512)
+        fail(UGKS_EINVAL, "gather_threads must be 0, 256 or 512");
+    if (p->gather_threads == 512 && (p->precision != UGKS_FP32 || p->vtile > 64))
+        fail(UGKS_EINVAL, "gather_threads = 512 needs UGKS_FP32 and vtile <= 64");
 }
 
 // invert the DxD normal matrix by its adjugate
@@ -680,6 +684,7 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     dc.res_part = (double *)c->dalloc((size_t)c->n_res_blocks * 2 * M * sizeof(double));
     dc.flags = c->flags_d;
     dc.P = c->P;
+    dc.nth = c->nth;
     dc.n_patches = c->n_patches;
     dc.n_vt = c->n_vt;
     dc.vtile = c->vtile;
@@ -691,28 +696,33 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
 
 namespace {
 
-// Autotuner of the gather tiling: the patch size and the velocity tile are
-// chosen by timing the gather kernel itself on this case (it writes only f~
+// Autotuner of the gather tiling: the patch size, the velocity tile and the
+// threads per CTA are chosen by timing the gather kernel itself on this case (it writes only f~
 // and scratch, so the state is untouched), and the choice is cached per
 // (dimension, precision, velocity count, mesh-size bucket) for later cases of
 // the same shape.
+struct Tiling {
+    int P = 0, vtile = 0, nth = 256;
+};
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tune_cache;
+std::map<std::string, Tiling> g_tune_cache;
 
 // velocity tile used when neither the caller nor the autotuner sets one
 int kDefaultVtile(int prec) { return prec == UGKS_FP64 ? 32 : 64; }
 
 template <typename T>
-void set_tiling(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, int vtile, size_t smem)
+void set_tiling(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, int vtile, int nth, size_t smem)
 {
     c->P = P;
     c->n_patches = (int)((c->C + P - 1) / P);
     c->vtile = vtile;
+    c->nth = nth;
     c->n_vt = (int)(c->nvp / vtile);
     c->cfg.smem = smem;
     dc.P = P;
     dc.n_patches = c->n_patches;
     dc.vtile = vtile;
+    dc.nth = nth;
     dc.n_vt = c->n_vt;
     dc.ring_ptr = c->upload(h.ring_ptr);
     dc.ring_cells = c->upload(h.ring_cells);
@@ -720,13 +730,13 @@ void set_tiling(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, int vt
 }
 
 template <typename T>
-void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tune_vtile)
+void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tune_vtile, bool tune_threads)
 {
     const size_t esz = sizeof(T);
     char key[160];
-    snprintf(key, sizeof(key), "D%d_nc%d_p%d_vt%d_nv%lld_c%d", c->D, c->NC, c->prec, tune_vtile ? 0 : c->vtile,
-             (long long)c->Nv, (int)std::lround(std::log2((double)c->C)));
-    std::pair<int, int> best(0, 0);
+    snprintf(key, sizeof(key), "D%d_nc%d_p%d_vt%d_t%d_nv%lld_c%d", c->D, c->NC, c->prec, tune_vtile ? 0 : c->vtile,
+             tune_threads ? 0 : c->nth, (long long)c->Nv, (int)std::lround(std::log2((double)c->C)));
+    Tiling best;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
@@ -734,7 +744,7 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
     }
     const int C = (int)c->C;
     auto smem_of = [&](const Host &hh, int vt) { return (size_t)hh.max_slope * c->NC * c->D * vt * esz; };
-    if (best.first == 0) {
+    if (best.P == 0) {
         // tetrahedra have more faces and larger rings than triangles, and one
         // stored component per velocity: smaller patches and wider velocity tiles
         const std::vector<int> pc = c->prec == UGKS_FP64 ? std::vector<int>{16, 24, 32, 48}
@@ -742,42 +752,47 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
                                                          : std::vector<int>{24, 32, 48, 64, 96};
         std::vector<int> vc = {c->vtile};
         if (tune_vtile) vc = c->D == 3 ? std::vector<int>{32, 64, 128} : std::vector<int>{32, 64};
+        // 512-thread CTAs (64 registers, two per SM) for FP32 at up to 64 velocities
+        std::vector<int> tc = {c->nth};
+        if (tune_threads) tc = c->prec == UGKS_FP32 ? std::vector<int>{256, 512} : std::vector<int>{256};
         cuda_ok(ugks::launch_pre_gather(dc, c->stream), "autotune prep");
         cudaEvent_t e0, e1;
         cuda_ok(cudaEventCreate(&e0), "event");
         cuda_ok(cudaEventCreate(&e1), "event");
         float best_ms = 0.f;
-        for (int vt : vc) {
-            if (c->nvp % vt) continue;
-            for (int P : pc) {
-                if (P > C && P != pc.front()) continue;
-                build_patches(h, C, P);
-                const size_t smem = smem_of(h, vt);
-                if (smem > (size_t)smem_max) continue;
-                set_tiling(c, dc, h, P, vt, smem);
-                cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
-                cuda_ok(cudaEventRecord(e0, c->stream), "event");
-                for (int r = 0; r < 2; ++r) cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
-                cuda_ok(cudaEventRecord(e1, c->stream), "event");
-                cuda_ok(cudaEventSynchronize(e1), "event");
-                float ms = 0.f;
-                cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "event");
-                if (best.first == 0 || ms < best_ms) {
-                    best = {P, vt};
-                    best_ms = ms;
+        for (int nth : tc)
+            for (int vt : vc) {
+                if (c->nvp % vt || (nth == 512 && vt > 64)) continue;
+                for (int P : pc) {
+                    if (P > C && P != pc.front()) continue;
+                    if (nth == 512 && P < 32) continue;          // 16 warps need work
+                    build_patches(h, C, P);
+                    const size_t smem = smem_of(h, vt);
+                    if (smem > (size_t)smem_max) continue;
+                    set_tiling(c, dc, h, P, vt, nth, smem);
+                    cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
+                    cuda_ok(cudaEventRecord(e0, c->stream), "event");
+                    for (int r = 0; r < 2; ++r) cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
+                    cuda_ok(cudaEventRecord(e1, c->stream), "event");
+                    cuda_ok(cudaEventSynchronize(e1), "event");
+                    float ms = 0.f;
+                    cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "event");
+                    if (best.P == 0 || ms < best_ms) {
+                        best = {P, vt, nth};
+                        best_ms = ms;
+                    }
                 }
             }
-        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        if (best.first == 0) return;                 // keep the default tiling
+        if (best.P == 0) return;                 // keep the default tiling
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune_cache[key] = best;
     }
-    if (best.first != c->P || best.second != c->vtile) {
-        build_patches(h, C, best.first);
-        const size_t smem = smem_of(h, best.second);
-        if (smem <= (size_t)smem_max) set_tiling(c, dc, h, best.first, best.second, smem);
+    if (best.P != c->P || best.vtile != c->vtile || best.nth != c->nth) {
+        build_patches(h, C, best.P);
+        const size_t smem = smem_of(h, best.vtile);
+        if (smem <= (size_t)smem_max) set_tiling(c, dc, h, best.P, best.vtile, best.nth, smem);
     }
 }
 
@@ -847,6 +862,7 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         // velocity rows are padded to a multiple of the widest tile the autotuner
         // may choose (64 in 2D, 128 in 3D) unless the tile is fixed
         c->vtile = params->vtile > 0 ? params->vtile : kDefaultVtile(c->prec);
+        c->nth = params->gather_threads > 0 ? params->gather_threads : 256;
         const int vpad = params->vtile > 0 ? params->vtile : (c->D == 3 ? 128 : 64);
         int P = params->patch_cells > 0 ? params->patch_cells : (c->prec == UGKS_FP64 ? 32 : 48);
         Host h;
@@ -891,11 +907,13 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         if (c->prec == UGKS_FP64) {
             fill_case<double>(c.get(), c->d64, mesh, vgrid, params, h);
             cuda_ok(ugks::launch_init(c->d64, c->stream), "init");
-            if (params->patch_cells == 0) autotune<double>(c.get(), c->d64, h, smem_max, params->vtile == 0);
+            if (params->patch_cells == 0)
+                autotune<double>(c.get(), c->d64, h, smem_max, params->vtile == 0, params->gather_threads == 0);
         } else {
             fill_case<float>(c.get(), c->d32, mesh, vgrid, params, h);
             cuda_ok(ugks::launch_init(c->d32, c->stream), "init");
-            if (params->patch_cells == 0) autotune<float>(c.get(), c->d32, h, smem_max, params->vtile == 0);
+            if (params->patch_cells == 0)
+                autotune<float>(c.get(), c->d32, h, smem_max, params->vtile == 0, params->gather_threads == 0);
         }
         cuda_ok(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "create sync");
     });
@@ -1168,6 +1186,7 @@ ugks_status ugks_info(const ugks_case *c, ugks_info_t *info)
         info->n_patches = c->n_patches;
         info->patch_cells = c->P;
         info->vtile = c->vtile;
+        info->gather_threads = c->nth;
         info->kernel_launches_per_step = 5 + (c->F > 0 ? 5 : 0) + (c->NW > 0 ? 1 : 0);
         info->n_wall_faces = c->NW;
     });
@@ -1183,7 +1202,7 @@ struct ugks_batch {
     void *dcases = nullptr;         // device array of DevCase<T>
     // one persistent gather launch per velocity tile present in the batch
     struct Group {
-        int vtile = 0, nwork = 0, grid = 0;
+        int vtile = 0, nth = 256, nwork = 0, grid = 0;
         int4 *work = nullptr;
         size_t smem = 0;
     };
@@ -1214,16 +1233,21 @@ void batch_build(ugks_batch *b)
     for (int i = 0; i < n; ++i) h[i] = dc_of<T>(b->cases[i]);
     cuda_ok(cudaMalloc(&b->dcases, sizeof(ugks::DevCase<T>) * n), "batch alloc");
     cuda_ok(cudaMemcpy(b->dcases, h.data(), sizeof(ugks::DevCase<T>) * n, cudaMemcpyHostToDevice), "batch upload");
-    std::vector<int> tiles;
+    // one persistent launch per (velocity tile, threads per CTA) in the batch
+    std::vector<std::pair<int, int>> tiles;
     for (auto *c : b->cases)
-        if (std::find(tiles.begin(), tiles.end(), c->vtile) == tiles.end()) tiles.push_back(c->vtile);
-    for (int vtile : tiles) {
+        if (std::find(tiles.begin(), tiles.end(), std::make_pair(c->vtile, c->nth)) == tiles.end())
+            tiles.push_back({c->vtile, c->nth});
+    for (const auto &tt : tiles) {
+        const int vtile = tt.first, nth = tt.second;
+        auto in_group = [&](const ugks_case *c) { return c->vtile == vtile && c->nth == nth; };
         ugks_batch::Group g;
         g.vtile = vtile;
+        g.nth = nth;
         std::vector<int4> work;
         int max_vt = 0;
         for (int i = 0; i < n; ++i)
-            if (b->cases[i]->vtile == vtile) {
+            if (in_group(b->cases[i])) {
                 g.smem = std::max(g.smem, b->cases[i]->cfg.smem);
                 max_vt = std::max(max_vt, b->cases[i]->n_vt);
             }
@@ -1231,14 +1255,14 @@ void batch_build(ugks_batch *b)
         // on neighbouring patches of one case and tile, as in the single-case grid
         for (int vt = 0; vt < max_vt; ++vt)
             for (int i = 0; i < n; ++i) {
-                if (b->cases[i]->vtile != vtile || vt >= b->cases[i]->n_vt) continue;
+                if (!in_group(b->cases[i]) || vt >= b->cases[i]->n_vt) continue;
                 for (int pi = 0; pi < b->cases[i]->n_patches; ++pi) work.push_back(make_int4(i, pi, vt, 0));
             }
         cuda_ok(cudaMalloc((void **)&g.work, sizeof(int4) * std::max<size_t>(1, work.size())), "batch alloc");
         b->groups.push_back(g);      // owned by the batch from here on
         cuda_ok(cudaMemcpy(g.work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice), "batch upload");
         b->groups.back().nwork = (int)work.size();
-        b->groups.back().grid = std::min((int)work.size(), ugks::gather_resident_ctas<T>(b->D, vtile, g.smem));
+        b->groups.back().grid = std::min((int)work.size(), ugks::gather_resident_ctas<T>(b->D, vtile, nth, g.smem));
     }
 }
 
@@ -1256,8 +1280,8 @@ void batch_capture(ugks_batch *b)
         cuda_ok(cudaStreamWaitEvent(st, b->join[k], 0), "join wait");
     }
     for (const auto &g : b->groups)
-        cuda_ok(ugks::launch_gather_batch<T>(b->D, g.vtile, (const ugks::DevCase<T> *)b->dcases, g.work, g.nwork,
-                                             g.grid, g.smem, st),
+        cuda_ok(ugks::launch_gather_batch<T>(b->D, g.vtile, g.nth, (const ugks::DevCase<T> *)b->dcases, g.work,
+                                             g.nwork, g.grid, g.smem, st),
                 "batched gather");
     cuda_ok(cudaEventRecord(b->fork2, st), "fork");
     for (int k = 0; k < ugks_batch::NB; ++k) cuda_ok(cudaStreamWaitEvent(b->br[k], b->fork2, 0), "fork wait");

@@ -1229,8 +1229,13 @@ __device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, c
     }
 }
 
-template <typename T, int D, int NC, int TV>
-__global__ void __launch_bounds__(256) k_gather(DevCase<T> dc)
+// NTH threads per CTA; 512-thread CTAs are held to 64 registers so that two
+// fit an SM (32 resident warps, against 24 for 256-thread CTAs at 80).  A
+// minimum of 0 blocks leaves 256-thread CTAs to ptxas's own register choice:
+// an explicit 1 lets it take 113 registers in the 2D FP32 kernel, which
+// drops the SM to two CTAs and costs about 20 %.
+template <typename T, int D, int NC, int TV, int NTH>
+__global__ void __launch_bounds__(NTH, NTH >= 512 ? 2 : 0) k_gather(DevCase<T> dc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     gather_item<T, D, NC, TV>(dc, blockIdx.x, blockIdx.y, reinterpret_cast<T *>(smem_raw));
@@ -1239,9 +1244,9 @@ __global__ void __launch_bounds__(256) k_gather(DevCase<T> dc)
 // Persistent gather over many cases: a fixed grid of CTAs walks a work list of
 // (case, patch, velocity tile) items; each item is exactly the CTA of k_gather
 // for that case, so every case gets bit-identical results alone or batched.
-template <typename T, int D, int NC, int TV>
-__global__ void __launch_bounds__(256) k_gather_batch(const DevCase<T> *__restrict__ cases, const int4 *__restrict__ work,
-                                                      int nwork)
+template <typename T, int D, int NC, int TV, int NTH>
+__global__ void __launch_bounds__(NTH, NTH >= 512 ? 2 : 0) k_gather_batch(const DevCase<T> *__restrict__ cases,
+                                                                          const int4 *__restrict__ work, int nwork)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
@@ -1460,15 +1465,35 @@ __global__ void k_check(const double *W, int n, int M, int *flags)
 // ------------------------------------------------------------ launchers
 static inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
 
-template <typename T, int D, int NC, int TV>
+template <typename T, int D, int NC, int TV, int NTH>
 static cudaError_t gather_launch(const DevCase<T> &dc, size_t smem, cudaStream_t st)
 {
-    auto kern = k_gather<T, D, NC, TV>;
+    auto kern = k_gather<T, D, NC, TV, NTH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid(dc.n_patches, dc.n_vt);
-    kern<<<grid, 256, smem, st>>>(dc);
+    kern<<<grid, NTH, smem, st>>>(dc);
     return cudaGetLastError();
+}
+
+// the gather kernel of a case: velocities per lane TV = vtile / 32 and
+// threads per CTA (256, or 512 for FP32 at TV <= 2)
+template <typename T, int D, int NC>
+static cudaError_t gather_dispatch(const DevCase<T> &dc, size_t smem, cudaStream_t st)
+{
+    const int tv = dc.vtile / 32;
+    if (dc.nth == 512) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (tv == 1) return gather_launch<T, D, NC, 1, 512>(dc, smem, st);
+            if (tv == 2) return gather_launch<T, D, NC, 2, 512>(dc, smem, st);
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (dc.nth != 256) return cudaErrorInvalidValue;
+    if (tv == 1) return gather_launch<T, D, NC, 1, 256>(dc, smem, st);
+    if (tv == 2) return gather_launch<T, D, NC, 2, 256>(dc, smem, st);
+    if (tv == 4) return gather_launch<T, D, NC, 4, 256>(dc, smem, st);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T, int D, int NC>
@@ -1521,13 +1546,7 @@ template <typename T, int D, int NC>
 static cudaError_t step_dn(const DevCase<T> &dc, const StepConfig &cfg, cudaStream_t st, cudaEvent_t *ev)
 {
     pre_gather<T, D, NC>(dc, st, ev);
-    cudaError_t e;
-    switch (dc.vtile / 32) {
-    case 1: e = gather_launch<T, D, NC, 1>(dc, cfg.smem, st); break;
-    case 2: e = gather_launch<T, D, NC, 2>(dc, cfg.smem, st); break;
-    case 4: e = gather_launch<T, D, NC, 4>(dc, cfg.smem, st); break;
-    default: return cudaErrorInvalidValue;
-    }
+    cudaError_t e = gather_dispatch<T, D, NC>(dc, cfg.smem, st);
     if (e != cudaSuccess) return e;
     post_gather<T, D, NC>(dc, cfg, st, ev);
     return cudaGetLastError();
@@ -1552,62 +1571,72 @@ cudaError_t launch_post_gather(const DevCase<T> &dc, const StepConfig &cfg, cuda
 template <typename T>
 cudaError_t launch_gather(const DevCase<T> &dc, size_t smem, cudaStream_t st)
 {
-    const int tv = dc.vtile / 32;
-    if (dc.D == 2) {
-        if (tv == 1) return gather_launch<T, 2, 2, 1>(dc, smem, st);
-        if (tv == 2) return gather_launch<T, 2, 2, 2>(dc, smem, st);
-        if (tv == 4) return gather_launch<T, 2, 2, 4>(dc, smem, st);
-    } else {
-        if (tv == 1) return gather_launch<T, 3, 1, 1>(dc, smem, st);
-        if (tv == 2) return gather_launch<T, 3, 1, 2>(dc, smem, st);
-        if (tv == 4) return gather_launch<T, 3, 1, 4>(dc, smem, st);
-    }
-    return cudaErrorInvalidValue;
+    if (dc.D == 2) return gather_dispatch<T, 2, 2>(dc, smem, st);
+    return gather_dispatch<T, 3, 1>(dc, smem, st);
 }
 
-template <typename T, int D, int NC, int TV>
+template <typename T, int D, int NC, int TV, int NTH>
 static cudaError_t gather_batch_launch(const DevCase<T> *cases, const int4 *work, int nwork, int grid, size_t smem,
                                        cudaStream_t st)
 {
-    auto kern = k_gather_batch<T, D, NC, TV>;
+    auto kern = k_gather_batch<T, D, NC, TV, NTH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, 256, smem, st>>>(cases, work, nwork);
+    kern<<<grid, NTH, smem, st>>>(cases, work, nwork);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_gather_batch(int D, int vtile, const DevCase<T> *cases, const int4 *work, int nwork, int grid,
-                                size_t smem, cudaStream_t st)
+template <typename T, int D, int NC>
+static cudaError_t gather_batch_dispatch(int vtile, int nth, const DevCase<T> *cases, const int4 *work, int nwork,
+                                         int grid, size_t smem, cudaStream_t st)
 {
     const int tv = vtile / 32;
-    if (D == 2) {
-        if (tv == 1) return gather_batch_launch<T, 2, 2, 1>(cases, work, nwork, grid, smem, st);
-        if (tv == 2) return gather_batch_launch<T, 2, 2, 2>(cases, work, nwork, grid, smem, st);
-        if (tv == 4) return gather_batch_launch<T, 2, 2, 4>(cases, work, nwork, grid, smem, st);
-    } else {
-        if (tv == 1) return gather_batch_launch<T, 3, 1, 1>(cases, work, nwork, grid, smem, st);
-        if (tv == 2) return gather_batch_launch<T, 3, 1, 2>(cases, work, nwork, grid, smem, st);
-        if (tv == 4) return gather_batch_launch<T, 3, 1, 4>(cases, work, nwork, grid, smem, st);
+    if (nth == 512) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (tv == 1) return gather_batch_launch<T, D, NC, 1, 512>(cases, work, nwork, grid, smem, st);
+            if (tv == 2) return gather_batch_launch<T, D, NC, 2, 512>(cases, work, nwork, grid, smem, st);
+        }
+        return cudaErrorInvalidValue;
     }
+    if (nth != 256) return cudaErrorInvalidValue;
+    if (tv == 1) return gather_batch_launch<T, D, NC, 1, 256>(cases, work, nwork, grid, smem, st);
+    if (tv == 2) return gather_batch_launch<T, D, NC, 2, 256>(cases, work, nwork, grid, smem, st);
+    if (tv == 4) return gather_batch_launch<T, D, NC, 4, 256>(cases, work, nwork, grid, smem, st);
     return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_gather_batch(int D, int vtile, int nth, const DevCase<T> *cases, const int4 *work, int nwork,
+                                int grid, size_t smem, cudaStream_t st)
+{
+    if (D == 2) return gather_batch_dispatch<T, 2, 2>(vtile, nth, cases, work, nwork, grid, smem, st);
+    return gather_batch_dispatch<T, 3, 1>(vtile, nth, cases, work, nwork, grid, smem, st);
 }
 
 // CTAs of the gather kernel that fit on the device at once (persistent grid)
 template <typename T>
-int gather_resident_ctas(int D, int vtile, size_t smem)
+int gather_resident_ctas(int D, int vtile, int nth, size_t smem)
 {
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int tv = vtile / 32;
     const void *fn = nullptr;
-    if (D == 2) fn = tv == 1 ? (const void *)k_gather_batch<T, 2, 2, 1> : tv == 2 ? (const void *)k_gather_batch<T, 2, 2, 2>
-                                                                               : (const void *)k_gather_batch<T, 2, 2, 4>;
-    else fn = tv == 1 ? (const void *)k_gather_batch<T, 3, 1, 1> : tv == 2 ? (const void *)k_gather_batch<T, 3, 1, 2>
-                                                                      : (const void *)k_gather_batch<T, 3, 1, 4>;
+    if (nth == 512 && std::is_same<T, float>::value) {
+        if (D == 2) fn = tv == 1 ? (const void *)k_gather_batch<T, 2, 2, 1, 512> : (const void *)k_gather_batch<T, 2, 2, 2, 512>;
+        else fn = tv == 1 ? (const void *)k_gather_batch<T, 3, 1, 1, 512> : (const void *)k_gather_batch<T, 3, 1, 2, 512>;
+    } else {
+        if (D == 2)
+            fn = tv == 1   ? (const void *)k_gather_batch<T, 2, 2, 1, 256>
+                 : tv == 2 ? (const void *)k_gather_batch<T, 2, 2, 2, 256>
+                           : (const void *)k_gather_batch<T, 2, 2, 4, 256>;
+        else
+            fn = tv == 1   ? (const void *)k_gather_batch<T, 3, 1, 1, 256>
+                 : tv == 2 ? (const void *)k_gather_batch<T, 3, 1, 2, 256>
+                           : (const void *)k_gather_batch<T, 3, 1, 4, 256>;
+    }
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, nth, smem);
     return std::max(1, per) * std::max(1, nsm);
 }
 
@@ -1698,10 +1727,12 @@ template cudaError_t launch_post_gather<double>(const DevCase<double> &, const S
 template cudaError_t launch_post_gather<float>(const DevCase<float> &, const StepConfig &, cudaStream_t);
 template cudaError_t launch_gather<double>(const DevCase<double> &, size_t, cudaStream_t);
 template cudaError_t launch_gather<float>(const DevCase<float> &, size_t, cudaStream_t);
-template cudaError_t launch_gather_batch<double>(int, int, const DevCase<double> *, const int4 *, int, int, size_t, cudaStream_t);
-template cudaError_t launch_gather_batch<float>(int, int, const DevCase<float> *, const int4 *, int, int, size_t, cudaStream_t);
-template int gather_resident_ctas<double>(int, int, size_t);
-template int gather_resident_ctas<float>(int, int, size_t);
+template cudaError_t launch_gather_batch<double>(int, int, int, const DevCase<double> *, const int4 *, int, int, size_t,
+                                                 cudaStream_t);
+template cudaError_t launch_gather_batch<float>(int, int, int, const DevCase<float> *, const int4 *, int, int, size_t,
+                                                cudaStream_t);
+template int gather_resident_ctas<double>(int, int, int, size_t);
+template int gather_resident_ctas<float>(int, int, int, size_t);
 template cudaError_t launch_step<double>(const DevCase<double> &, const StepConfig &, cudaStream_t, cudaEvent_t *);
 template cudaError_t launch_step<float>(const DevCase<float> &, const StepConfig &, cudaStream_t, cudaEvent_t *);
 template cudaError_t launch_init<double>(const DevCase<double> &, cudaStream_t);

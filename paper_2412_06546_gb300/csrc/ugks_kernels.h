@@ -21,11 +21,11 @@ template <typename T> cudaError_t launch_pre_gather(const DevCase<T> &dc, cudaSt
 template <typename T> cudaError_t launch_post_gather(const DevCase<T> &dc, const StepConfig &cfg, cudaStream_t st);
 template <typename T> cudaError_t launch_gather(const DevCase<T> &dc, size_t smem, cudaStream_t st);
 // persistent gather over a work list of int4 (case, patch, velocity tile, 0) items;
-// cases[] is a device array of DevCase with the same D and vtile
+// cases[] is a device array of DevCase with the same D, vtile and threads per CTA
 template <typename T>
-cudaError_t launch_gather_batch(int D, int vtile, const DevCase<T> *cases, const int4 *work, int nwork, int grid,
-                                size_t smem, cudaStream_t st);
-template <typename T> int gather_resident_ctas(int D, int vtile, size_t smem);
+cudaError_t launch_gather_batch(int D, int vtile, int nth, const DevCase<T> *cases, const int4 *work, int nwork,
+                                int grid, size_t smem, cudaStream_t st);
+template <typename T> int gather_resident_ctas(int D, int vtile, int nth, size_t smem);
 template <typename T> cudaError_t launch_heatflux(const DevCase<T> &dc, cudaStream_t st);
 template <typename T>
 cudaError_t launch_f_export(const DevCase<T> &dc, const long long *perm, int c0, int nc, double *out, cudaStream_t st);

@@ -136,9 +136,10 @@ ugks_status create_case(ugks_server *s, Request *r)
     p.wall_T = r->wall_T.empty() ? nullptr : r->wall_T.data();
     p.wall_U = r->wall_U.empty() ? nullptr : r->wall_U.data();
     p.prim_init = r->has_init ? r->prim_init.data() : nullptr;
-    // one velocity tile for every case of a precision, so that all of them
-    // share one batched gather launch
+    // one velocity tile and one block size for every case of a precision, so
+    // that all of them share one batched gather launch
     if (p.vtile == 0) p.vtile = p.precision == UGKS_FP64 ? 32 : 64;
+    if (p.gather_threads == 0) p.gather_threads = 256;
     return ugks_create(&m, &v, &p, nullptr, (void *)s->stream, &r->c);
 }
 

@@ -130,3 +130,18 @@ def test_no_cpu_fallback_without_library(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
         finally:
             _lib._lib = saved
+
+
+@pytest.mark.parametrize("precision,threads,vtile,msg", [
+    (_lib.FP32, 128, 0, b"gather_threads must be 0, 256 or 512"),
+    (_lib.FP64, 512, 0, b"gather_threads = 512 needs UGKS_FP32"),
+    (_lib.FP32, 512, 128, b"gather_threads = 512 needs UGKS_FP32"),
+])
+def test_gather_block_size_is_validated(lib, precision, threads, vtile, msg):
+    from paper_2412_06546_gb300 import cases
+    case = cases.cavity_case(n=3, nv=4)
+    (m, v, p), keep = _lib.make_structs(case["mesh"], case["vgrid"], case["params"], case["init"],
+                                        precision, 0, vtile, threads)
+    h = ct.c_void_p()
+    assert lib.ugks_create(ct.byref(m), ct.byref(v), ct.byref(p), None, None, ct.byref(h)) == 1
+    assert msg in lib.ugks_last_error() and not h.value

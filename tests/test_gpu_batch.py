@@ -64,12 +64,13 @@ def test_batch_3d_and_interleaving_with_single_steps():
 
 
 def test_batch_with_mixed_velocity_tiles():
-    """Cases tiled with 32, 64 and 128 velocities per CTA in one batch (one
-    persistent launch per tile width) match the same cases stepped alone."""
+    """Cases tiled with 32, 64 and 128 velocities per CTA, and 256- or
+    512-thread CTAs, in one batch (one persistent launch per tile width and
+    block size) match the same cases stepped alone."""
     specs = _cases2d()[:3]
-    tiles = [(24, 32), (48, 64), (16, 128)]
+    tiles = [(24, 32, 256), (48, 64, 512), (16, 128, 256)]
     mk = lambda c, t: _lib.Case(c["mesh"], c["vgrid"], c["params"], c["init"], precision=_lib.FP32,
-                                patch_cells=t[0], vtile=t[1])
+                                patch_cells=t[0], vtile=t[1], threads=t[2])
     alone = [mk(c, t) for c, t in zip(specs, tiles)]
     for g in alone:
         g.step(4)

@@ -325,6 +325,26 @@ def test_tiling_does_not_change_results(patch, vtile):
     _compare(o, g, what=f"tiling {patch}/{vtile}")
 
 
+@pytest.mark.parametrize("patch,vtile,threads", [(32, 32, 512), (48, 64, 512), (40, 64, 256)])
+def test_fp32_gather_block_sizes(patch, vtile, threads):
+    """The FP32 gather with 256- and 512-thread CTAs (one, two or four
+    velocities per lane) against the oracle: one step from an
+    FP32-representable perturbed state, 1e-5 of max |f| per element."""
+    case = cs.cylinder_case(n_cells=1500, nvx=18, nvy=15, mach=4.0)
+    o, g = _pair(case, precision=_lib.FP32, perturb=0.05, patch_cells=patch, vtile=vtile, threads=threads)
+    f0, W0, _ = o.state()
+    f0 = f0.astype(np.float32).astype(np.float64)
+    o.set_state(f0, W0)
+    g.set_state(f0, W0)
+    info = g.info()
+    assert info["gather_threads"] == threads and info["vtile"] == vtile
+    o.step(1)
+    g.step(1)
+    fo, Wo, _ = o.state()
+    fg, Wg = g.state()
+    assert _rel_max(fg, fo) <= 1e-5 and _rel_max(Wg, Wo) <= 1e-5, (_rel_max(fg, fo), _rel_max(Wg, Wo))
+
+
 def test_runs_are_bitwise_deterministic():
     case = cs.cylinder_case(n_cells=1500, nvx=16, nvy=14)
     outs = []
