@@ -180,9 +180,22 @@ ugks_status ugks_wall_quantities(ugks_case *c, int64_t *face, double *p, double 
 ugks_status ugks_get_cells(ugks_case *c, const int64_t *cells, int64_t n, double *f, double *W);
 
 /* Replace the state from host buffers (same layout); either may be NULL.
- * The heat flux is recomputed from the new f.  Asynchronous with respect to
- * the host after the upload is issued. */
+ * The heat flux is recomputed from the new f.  The call returns once the
+ * copies and kernels are queued: f is copied in chunks on a stream of the case
+ * that overlaps the reordering of earlier chunks on the case stream, and the
+ * case stream waits for every chunk.  Page-locked host buffers must stay
+ * unchanged until the case stream has passed the upload (any synchronising
+ * call, e.g. ugks_moments or ugks_check); pageable ones are read before the
+ * call returns. */
 ugks_status ugks_set_state(ugks_case *c, const double *f, const double *W);
+
+/* ugks_get_state and ugks_set_state with f in single precision:
+ * f[C][ncomp][nv] FP32 in caller cell order, W still FP64.  For a UGKS_FP32
+ * case they move the stored values exactly with half the bytes of the FP64
+ * calls; for a UGKS_FP64 case f is rounded to nearest on the way out and
+ * widened exactly on the way in.  Same synchronisation as the FP64 calls. */
+ugks_status ugks_get_state_f32(ugks_case *c, float *f, double *W);
+ugks_status ugks_set_state_f32(ugks_case *c, const float *f, const double *W);
 
 /* Kernel-group timing.  After ugks_profile_begin(c, max_steps) the next
  * max_steps calls of ugks_step record CUDA events on the case stream around

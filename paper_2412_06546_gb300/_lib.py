@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libugks.so")
 
 D_P = ct.POINTER(ct.c_double)
+F_P = ct.POINTER(ct.c_float)
 I64_P = ct.POINTER(ct.c_int64)
 I32_P = ct.POINTER(ct.c_int32)
 
@@ -94,6 +95,8 @@ EXPORTS = {
     "ugks_residual": (ct.c_int, [ct.c_void_p, D_P]),
     "ugks_get_state": (ct.c_int, [ct.c_void_p, D_P, D_P]),
     "ugks_set_state": (ct.c_int, [ct.c_void_p, D_P, D_P]),
+    "ugks_get_state_f32": (ct.c_int, [ct.c_void_p, F_P, D_P]),
+    "ugks_set_state_f32": (ct.c_int, [ct.c_void_p, F_P, D_P]),
     "ugks_get_cells": (ct.c_int, [ct.c_void_p, I64_P, ct.c_int64, D_P, D_P]),
     "ugks_wall_quantities": (ct.c_int, [ct.c_void_p, I64_P, D_P, D_P, D_P]),
     "ugks_info": (ct.c_int, [ct.c_void_p, ct.POINTER(Info)]),
@@ -259,10 +262,16 @@ class Case:
         check(load().ugks_residual(self._h, _p(r)))
         return r
 
-    def state(self, with_f=True):
-        f = np.empty((self.C, self.nc, self.Nv)) if with_f else None
+    def state(self, with_f=True, f_dtype=np.float64):
+        """(f[C][ncomp][nv], W[C][dim+2]) in mesh order; f as FP64, or as
+        FP32 with ``f_dtype=np.float32`` (exact for FP32 storage)."""
+        single = np.dtype(f_dtype) == np.float32
+        f = np.empty((self.C, self.nc, self.Nv), np.float32 if single else np.float64) if with_f else None
         W = np.empty((self.C, self.D + 2))
-        check(load().ugks_get_state(self._h, _p(f), _p(W)))
+        if single:
+            check(load().ugks_get_state_f32(self._h, _p(f, F_P), _p(W)))
+        else:
+            check(load().ugks_get_state(self._h, _p(f), _p(W)))
         return f, W
 
     def wall_quantities(self):
@@ -283,9 +292,15 @@ class Case:
         return f, W
 
     def set_state(self, f=None, W=None):
-        fa = _c(f) if f is not None else None
+        """Replace f and/or W; an FP32 array f goes through the FP32 upload
+        (half the bytes), any other through the FP64 one.  A page-locked f
+        must stay unchanged until the next synchronising call."""
         Wa = _c(W) if W is not None else None
-        check(load().ugks_set_state(self._h, _p(fa), _p(Wa)))
+        if f is not None and np.asarray(f).dtype == np.float32:
+            check(load().ugks_set_state_f32(self._h, _p(_c(f, np.float32), F_P), _p(Wa)))
+        else:
+            fa = _c(f) if f is not None else None
+            check(load().ugks_set_state(self._h, _p(fa), _p(Wa)))
 
     def heat_flux(self):
         return self.moments()[3]

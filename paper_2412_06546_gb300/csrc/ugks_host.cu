@@ -71,6 +71,10 @@ struct ugks_case {
     // kernel-group profiling
     std::vector<cudaEvent_t> prof_ev;
     int prof_max = 0, prof_used = 0;
+    // host -> device copies of ugks_set_state (created on first use): the copy
+    // stream and its events (ready, copied[2], consumed[2])
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t io_ev[5] = {};
 
     void *dalloc(size_t bytes)
     {
@@ -105,6 +109,15 @@ struct ugks_case {
     {
         if (stream) cudaStreamSynchronize(stream);
         else cudaDeviceSynchronize();
+        if (copy_stream) {
+            cudaStreamSynchronize(copy_stream);
+            for (auto &e : io_ev) {
+                if (e) cudaEventDestroy(e);
+                e = nullptr;
+            }
+            cudaStreamDestroy(copy_stream);
+            copy_stream = nullptr;
+        }
         for (auto &b : blocks) {
             if (user_alloc) alloc.free(alloc.ctx, b.first, b.second, (void *)stream);
             else cudaFree(b.first);
@@ -823,6 +836,107 @@ auto with_dc(ugks_case *c, Fn &&fn)
     if (c->prec == UGKS_FP64) return fn(c->d64);
     return fn(c->d32);
 }
+
+// f of the case into host memory, f[C][ncomp][nv] of element type S in caller
+// cell order, staged through the f_nxt buffer in chunks of cells
+template <typename S>
+void export_f(ugks_case *c, S *f)
+{
+    const size_t per = (size_t)c->NC * c->Nv;
+    const size_t cap = c->f_bytes / sizeof(S);
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>(cap / per, (size_t)c->C));
+    for (int c0 = 0; c0 < (int)c->C; c0 += chunk) {
+        const int nc = (int)std::min<int64_t>(chunk, c->C - c0);
+        with_dc(c, [&](auto &dc) {
+            S *stg = (S *)dc.f_nxt;
+            cuda_ok(ugks::launch_f_export(dc, c->perm_d, c0, nc, stg, c->stream), "f export");
+            cuda_ok(cudaMemcpyAsync(f + (size_t)c0 * per, stg, (size_t)nc * per * sizeof(S), cudaMemcpyDeviceToHost,
+                                    c->stream),
+                    "f copy");
+            cuda_ok(cudaStreamSynchronize(c->stream), "sync");
+        });
+    }
+}
+
+// f from host memory (layout of export_f) into the case.  The f_nxt buffer is
+// split into two staging slots; chunks of cells alternate between them.  The
+// copy of a chunk runs on the case's copy stream while the case stream imports
+// (reorders and converts) the chunk before it; a slot is refilled only after
+// its previous import.  The first copy waits for the work already queued on
+// the case stream, which may still use f_nxt.
+template <typename S>
+void import_f(ugks_case *c, const S *f)
+{
+    const size_t per = (size_t)c->NC * c->Nv;
+    const size_t slot = c->f_bytes / 2 / sizeof(S);
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>(slot / per, (size_t)c->C));
+    chunk = std::min(chunk, (int)std::max<int64_t>(1, (c->C + 3) / 4));   // at least four chunks in flight
+    if (!c->copy_stream) {
+        cuda_ok(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "copy stream");
+        for (auto &e : c->io_ev) cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create");
+    }
+    cudaEvent_t ready = c->io_ev[0], *copied = c->io_ev + 1, *consumed = c->io_ev + 3;
+    cuda_ok(cudaEventRecord(ready, c->stream), "event");
+    cuda_ok(cudaStreamWaitEvent(c->copy_stream, ready, 0), "event wait");
+    int k = 0;
+    for (int c0 = 0; c0 < (int)c->C; c0 += chunk, ++k) {
+        const int nc = (int)std::min<int64_t>(chunk, c->C - c0);
+        const int sl = k & 1;
+        if (k >= 2) cuda_ok(cudaStreamWaitEvent(c->copy_stream, consumed[sl], 0), "event wait");
+        with_dc(c, [&](auto &dc) {
+            S *stg = (S *)dc.f_nxt + (size_t)sl * slot;
+            cuda_ok(cudaMemcpyAsync(stg, f + (size_t)c0 * per, (size_t)nc * per * sizeof(S), cudaMemcpyHostToDevice,
+                                    c->copy_stream),
+                    "f upload");
+            cuda_ok(cudaEventRecord(copied[sl], c->copy_stream), "event");
+            cuda_ok(cudaStreamWaitEvent(c->stream, copied[sl], 0), "event wait");
+            cuda_ok(ugks::launch_f_import(dc, c->perm_d, c0, nc, stg, c->stream), "f import");
+            cuda_ok(cudaEventRecord(consumed[sl], c->stream), "event");
+        });
+    }
+}
+
+// W[C][dim+2] (caller cell order) into the case through the gradW scratch
+void import_W(ugks_case *c, const double *W)
+{
+    const int D = c->D, M = D + 2;
+    double *Wd = c->prec == UGKS_FP64 ? c->d64.W : c->d32.W;
+    double *stg = c->prec == UGKS_FP64 ? c->d64.gradW : c->d32.gradW;
+    cuda_ok(cudaMemcpyAsync(stg, W, (size_t)c->C * M * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+            "W upload");
+    cuda_ok(ugks::launch_W_permute(stg, c->perm_d, (int)c->C, D, Wd, 1, c->stream), "W import");
+}
+
+void export_W(ugks_case *c, double *W)
+{
+    const int D = c->D, M = D + 2;
+    double *Wd = c->prec == UGKS_FP64 ? c->d64.W : c->d32.W;
+    double *stg = c->prec == UGKS_FP64 ? c->d64.gradW : c->d32.gradW;
+    cuda_ok(ugks::launch_W_permute(Wd, c->perm_d, (int)c->C, D, stg, 0, c->stream), "W export");
+    cuda_ok(cudaMemcpyAsync(W, stg, (size_t)c->C * M * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "W copy");
+    cuda_ok(cudaStreamSynchronize(c->stream), "sync");
+}
+
+template <typename S>
+ugks_status get_state(ugks_case *c, S *f, double *W)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        if (W) export_W(c, W);
+        if (f) export_f(c, f);
+    });
+}
+
+template <typename S>
+ugks_status set_state(ugks_case *c, const S *f, const double *W)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        if (W) import_W(c, W);
+        if (f) import_f(c, f);
+        if (f || W) with_dc(c, [&](auto &dc) { cuda_ok(ugks::launch_heatflux(dc, c->stream), "heat flux"); });
+    });
+}
 }  // namespace
 
 namespace ugks {
@@ -999,38 +1113,9 @@ ugks_status ugks_residual(ugks_case *c, double *res)
     });
 }
 
-ugks_status ugks_get_state(ugks_case *c, double *f, double *W)
-{
-    return guard([&] {
-        if (!c) fail(UGKS_EINVAL, "case is NULL");
-        const int D = c->D, M = D + 2;
-        if (W) {
-            double *Wd = c->prec == UGKS_FP64 ? c->d64.W : c->d32.W;
-            double *stg = c->prec == UGKS_FP64 ? c->d64.gradW : c->d32.gradW;
-            cuda_ok(ugks::launch_W_permute(Wd, c->perm_d, (int)c->C, D, stg, 0, c->stream), "W export");
-            cuda_ok(cudaMemcpyAsync(W, stg, (size_t)c->C * M * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-                    "W copy");
-            cuda_ok(cudaStreamSynchronize(c->stream), "sync");
-        }
-        if (f) {
-            // stage through the f_nxt buffer in chunks of cells
-            const size_t per = (size_t)c->NC * c->Nv;
-            const size_t cap = c->f_bytes / sizeof(double);
-            const int chunk = (int)std::max<size_t>(1, std::min<size_t>(cap / per, (size_t)c->C));
-            for (int c0 = 0; c0 < (int)c->C; c0 += chunk) {
-                const int nc = (int)std::min<int64_t>(chunk, c->C - c0);
-                with_dc(c, [&](auto &dc) {
-                    double *stg = (double *)dc.f_nxt;
-                    cuda_ok(ugks::launch_f_export(dc, c->perm_d, c0, nc, stg, c->stream), "f export");
-                    cuda_ok(cudaMemcpyAsync(f + (size_t)c0 * per, stg, (size_t)nc * per * sizeof(double),
-                                            cudaMemcpyDeviceToHost, c->stream),
-                            "f copy");
-                    cuda_ok(cudaStreamSynchronize(c->stream), "sync");
-                });
-            }
-        }
-    });
-}
+ugks_status ugks_get_state(ugks_case *c, double *f, double *W) { return get_state(c, f, W); }
+
+ugks_status ugks_get_state_f32(ugks_case *c, float *f, double *W) { return get_state(c, f, W); }
 
 ugks_status ugks_wall_quantities(ugks_case *c, int64_t *face, double *p, double *sigma, double *q)
 {
@@ -1105,36 +1190,9 @@ ugks_status ugks_get_cells(ugks_case *c, const int64_t *cells, int64_t n, double
     });
 }
 
-ugks_status ugks_set_state(ugks_case *c, const double *f, const double *W)
-{
-    return guard([&] {
-        if (!c) fail(UGKS_EINVAL, "case is NULL");
-        const int D = c->D, M = D + 2;
-        if (W) {
-            double *Wd = c->prec == UGKS_FP64 ? c->d64.W : c->d32.W;
-            double *stg = c->prec == UGKS_FP64 ? c->d64.gradW : c->d32.gradW;
-            cuda_ok(cudaMemcpyAsync(stg, W, (size_t)c->C * M * sizeof(double), cudaMemcpyHostToDevice, c->stream),
-                    "W upload");
-            cuda_ok(ugks::launch_W_permute(stg, c->perm_d, (int)c->C, D, Wd, 1, c->stream), "W import");
-        }
-        if (f) {
-            const size_t per = (size_t)c->NC * c->Nv;
-            const size_t cap = c->f_bytes / sizeof(double);
-            const int chunk = (int)std::max<size_t>(1, std::min<size_t>(cap / per, (size_t)c->C));
-            for (int c0 = 0; c0 < (int)c->C; c0 += chunk) {
-                const int nc = (int)std::min<int64_t>(chunk, c->C - c0);
-                with_dc(c, [&](auto &dc) {
-                    double *stg = (double *)dc.f_nxt;
-                    cuda_ok(cudaMemcpyAsync(stg, f + (size_t)c0 * per, (size_t)nc * per * sizeof(double),
-                                            cudaMemcpyHostToDevice, c->stream),
-                            "f upload");
-                    cuda_ok(ugks::launch_f_import(dc, c->perm_d, c0, nc, stg, c->stream), "f import");
-                });
-            }
-        }
-        if (f || W) with_dc(c, [&](auto &dc) { cuda_ok(ugks::launch_heatflux(dc, c->stream), "heat flux"); });
-    });
-}
+ugks_status ugks_set_state(ugks_case *c, const double *f, const double *W) { return set_state(c, f, W); }
+
+ugks_status ugks_set_state_f32(ugks_case *c, const float *f, const double *W) { return set_state(c, f, W); }
 
 ugks_status ugks_profile_begin(ugks_case *c, int32_t max_steps)
 {

@@ -1392,10 +1392,12 @@ __global__ void k_collide(DevCase<T> dc)
 }
 
 // ------------------------------------------------------------ state I/O
-template <typename T, int D, int NC>
-__global__ void k_f_export(DevCase<T> dc, const long long *perm, int c0, int nc, double *out)
+// Host-layout element type S: double, or float for callers that hold the
+// distribution in single precision (exact for FP32 storage).
+template <typename T, int D, int NC, typename S>
+__global__ void k_f_export(DevCase<T> dc, const long long *perm, int c0, int nc, S *out)
 {
-    // out[(i - c0)][m][k] (FP64, caller cell order i) from internal cell perm_inv...
+    // out[(i - c0)][m][k] (caller cell order i) from internal cell perm[i]
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long per = (long long)NC * dc.nv;
     if (idx >= (long long)nc * per) return;
@@ -1403,11 +1405,11 @@ __global__ void k_f_export(DevCase<T> dc, const long long *perm, int c0, int nc,
     const long long r = idx % per;
     const int m = (int)(r / dc.nv), k = (int)(r % dc.nv);
     const long long ci = perm[i];
-    out[idx] = (double)dc.f_cur[(size_t)ci * NC * dc.nvp + (size_t)m * dc.nvp + k];
+    out[idx] = (S)dc.f_cur[(size_t)ci * NC * dc.nvp + (size_t)m * dc.nvp + k];
 }
 
-template <typename T, int D, int NC>
-__global__ void k_f_import(DevCase<T> dc, const long long *perm, int c0, int nc, const double *in)
+template <typename T, int D, int NC, typename S>
+__global__ void k_f_import(DevCase<T> dc, const long long *perm, int c0, int nc, const S *in)
 {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long per = (long long)NC * dc.nvp;
@@ -1667,25 +1669,24 @@ cudaError_t launch_heatflux(const DevCase<T> &dc, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_f_export(const DevCase<T> &dc, const long long *perm, int c0, int nc, double *out,
-                            cudaStream_t st)
+template <typename T, typename S>
+cudaError_t launch_f_export(const DevCase<T> &dc, const long long *perm, int c0, int nc, S *out, cudaStream_t st)
 {
     long long n = (long long)nc * (dc.D == 2 ? 2 : 1) * dc.nv;
     if (n == 0) return cudaSuccess;
-    if (dc.D == 2) k_f_export<T, 2, 2><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, out);
-    else k_f_export<T, 3, 1><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, out);
+    if (dc.D == 2) k_f_export<T, 2, 2, S><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, out);
+    else k_f_export<T, 3, 1, S><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, out);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_f_import(const DevCase<T> &dc, const long long *perm, int c0, int nc, const double *in,
+template <typename T, typename S>
+cudaError_t launch_f_import(const DevCase<T> &dc, const long long *perm, int c0, int nc, const S *in,
                             cudaStream_t st)
 {
     long long n = (long long)nc * (dc.D == 2 ? 2 : 1) * dc.nvp;
     if (n == 0) return cudaSuccess;
-    if (dc.D == 2) k_f_import<T, 2, 2><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, in);
-    else k_f_import<T, 3, 1><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, in);
+    if (dc.D == 2) k_f_import<T, 2, 2, S><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, in);
+    else k_f_import<T, 3, 1, S><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, in);
     return cudaGetLastError();
 }
 
@@ -1739,9 +1740,14 @@ template cudaError_t launch_init<double>(const DevCase<double> &, cudaStream_t);
 template cudaError_t launch_init<float>(const DevCase<float> &, cudaStream_t);
 template cudaError_t launch_heatflux<double>(const DevCase<double> &, cudaStream_t);
 template cudaError_t launch_heatflux<float>(const DevCase<float> &, cudaStream_t);
-template cudaError_t launch_f_export<double>(const DevCase<double> &, const long long *, int, int, double *, cudaStream_t);
-template cudaError_t launch_f_export<float>(const DevCase<float> &, const long long *, int, int, double *, cudaStream_t);
-template cudaError_t launch_f_import<double>(const DevCase<double> &, const long long *, int, int, const double *, cudaStream_t);
-template cudaError_t launch_f_import<float>(const DevCase<float> &, const long long *, int, int, const double *, cudaStream_t);
+#define UGKS_STATE_IO(T, S)                                                                                   \
+    template cudaError_t launch_f_export<T, S>(const DevCase<T> &, const long long *, int, int, S *, cudaStream_t); \
+    template cudaError_t launch_f_import<T, S>(const DevCase<T> &, const long long *, int, int, const S *,          \
+                                               cudaStream_t);
+UGKS_STATE_IO(double, double)
+UGKS_STATE_IO(double, float)
+UGKS_STATE_IO(float, double)
+UGKS_STATE_IO(float, float)
+#undef UGKS_STATE_IO
 
 }  // namespace ugks

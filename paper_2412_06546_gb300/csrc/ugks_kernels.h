@@ -27,10 +27,12 @@ cudaError_t launch_gather_batch(int D, int vtile, int nth, const DevCase<T> *cas
                                 int grid, size_t smem, cudaStream_t st);
 template <typename T> int gather_resident_ctas(int D, int vtile, int nth, size_t smem);
 template <typename T> cudaError_t launch_heatflux(const DevCase<T> &dc, cudaStream_t st);
-template <typename T>
-cudaError_t launch_f_export(const DevCase<T> &dc, const long long *perm, int c0, int nc, double *out, cudaStream_t st);
-template <typename T>
-cudaError_t launch_f_import(const DevCase<T> &dc, const long long *perm, int c0, int nc, const double *in, cudaStream_t st);
+// state I/O between the internal layout and a host-layout staging buffer of
+// element type S (double or float)
+template <typename T, typename S>
+cudaError_t launch_f_export(const DevCase<T> &dc, const long long *perm, int c0, int nc, S *out, cudaStream_t st);
+template <typename T, typename S>
+cudaError_t launch_f_import(const DevCase<T> &dc, const long long *perm, int c0, int nc, const S *in, cudaStream_t st);
 cudaError_t launch_residual(const double *res_part, int nblocks, int D, double *res, cudaStream_t st);
 cudaError_t launch_moments_out(const double *W, const double *q, const long long *perm, int C, int D, double *out,
                                cudaStream_t st);
