@@ -332,6 +332,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fp64-steps", type=int, default=0, help="steps of the FP64 plain path (0: steps/10)")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--ref-steps", type=int, default=0)
     ap.add_argument("--ref-warmup", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -392,7 +393,9 @@ def main():
 
     # e2e: state in pinned host memory -> ugks_set_state_f32 -> ugks_step -> ugks_moments
     f_host_bytes = C * nc * Nv * 4
-    if f_host_bytes > E2E_MAX_BYTES:
+    if args.no_e2e or args.e2e_steps < 1:
+        e2e = {"skipped": "not requested"}
+    elif f_host_bytes > E2E_MAX_BYTES:
         e2e = {"skipped": f"the host copy of f ({f_host_bytes / 1e9:.1f} GB) exceeds {E2E_MAX_BYTES / 1e9:.0f} GB"}
     else:
         e2e = _e2e(torch, g, args, dist, ws, C, Nv, info)

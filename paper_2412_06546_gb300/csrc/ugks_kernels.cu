@@ -603,24 +603,105 @@ __global__ void k_face_fin1(DevCase<T> dc)
 // number of unique entries of a symmetric (D+2)x(D+2) matrix
 template <int D> struct Sym { static constexpr int N = (D + 2) * (D + 3) / 2; };
 
-// unique entries of P_c(c) = int psi_c psi_c^T g0 dxi / H0, row-major upper triangle
-template <typename T, int D>
-__device__ __forceinline__ void psi_c_outer(const T c[D], T c2, T nb, T xb, T P[Sym<D>::N])
+// The sums the slope systems need on an unstructured velocity set are the
+// entries of sum_k w_k H0 psi_c psi_c^T and of the same with a factor c_d, with
+// psi_c = (1, c, psi_E) and, after integrating the internal degrees of freedom,
+// psi_E = (|c|^2 + nb) / 2 and psi_E^2 = (|c|^4 + 2 nb |c|^2 + xb) / 4.  Every
+// one of them is a combination of fewer distinct moments R of w H0:
+//   c^a for |a| <= 3 (1, c_d, pairs d <= e, triples d <= e <= g),
+//   |c|^2 c_d c_e (d <= e), |c|^4 and |c|^4 c_d,
+// 30 in 3D against 60 entries (16 against 30 in 2D).  k_face_sum2 reduces R;
+// k_face_fin2 forms the entries in FP64 (mono_moments).
+template <int D> struct Mono {
+    static constexpr int N2 = D * (D + 1) / 2;                // pairs d <= e
+    static constexpr int N3 = D * (D + 1) * (D + 2) / 6;      // triples d <= e <= g
+    static constexpr int O1 = 1, O2 = O1 + D, O3 = O2 + N2, OQ2 = O3 + N3, OQ4 = OQ2 + N2, N = OQ4 + 1 + D;
+};
+
+// position of the pair d <= e (row-major upper triangle) and of the triple
+// d <= e <= g (lexicographic), the order in which k_face_sum2 stores them
+__host__ __device__ constexpr int pair_index(int D, int d, int e) { return d * D - d * (d - 1) / 2 + (e - d); }
+
+__host__ __device__ constexpr int triple_index(int D, int d, int e, int g)
 {
+    // triples with a first index below d, then with (d, b < e), then (d, e, c < g)
+    return (D * (D + 1) * (D + 2) - (D - d) * (D - d + 1) * (D - d + 2)) / 6 +
+           ((D - d) * (D - d + 1) - (D - e) * (D - e + 1)) / 2 + (g - e);
+}
+
+// sum w H0 c_a c_b (c_g) from R, indices in any order
+template <int D> __device__ __forceinline__ double mono2(const double *R, int a, int b)
+{
+    return R[Mono<D>::O2 + (a <= b ? pair_index(D, a, b) : pair_index(D, b, a))];
+}
+
+template <int D> __device__ __forceinline__ double mono3(const double *R, int a, int b, int g)
+{
+    int x = a, y = b, z = g, t;
+    if (x > y) { t = x; x = y; y = t; }
+    if (y > z) { t = y; y = z; z = t; }
+    if (x > y) { t = x; x = y; y = t; }
+    return R[Mono<D>::O3 + triple_index(D, x, y, z)];
+}
+
+// the k_face_sum2 entries (layout of sep_moments) from the distinct moments R
+template <int D>
+__device__ void mono_moments(const double *R, double nb, double xb, double *S)
+{
+    using Mo = Mono<D>;
+    constexpr int NS = Sym<D>::N;
     constexpr int M = D + 2;
-    const T e = T(0.5) * (c2 + nb);                               // int psi_E g / H
-    const T ee = T(0.25) * (c2 * c2 + T(2) * nb * c2 + xb);       // int psi_E^2 g / H
-    T v[M];
-    v[0] = T(1);
-    for (int d = 0; d < D; ++d) v[1 + d] = c[d];
+    double s2 = 0.0, s2c[D];                        // sum |c|^2 and sum |c|^2 c_d
+#pragma unroll
+    for (int e = 0; e < D; ++e) s2 += mono2<D>(R, e, e);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        s2c[d] = 0.0;
+#pragma unroll
+        for (int e = 0; e < D; ++e) s2c[d] += mono3<D>(R, d, e, e);
+    }
     int t = 0;
+#pragma unroll
     for (int i = 0; i < M; ++i)
+#pragma unroll
         for (int j = i; j < M; ++j) {
-            T val;
-            if (j < M - 1) val = v[i] * v[j];
-            else if (i < M - 1) val = v[i] * e;
-            else val = ee;
-            P[t++] = val;
+            double base, bc[D];
+            if (j < M - 1) {                        // psi_i psi_j: a monomial of degree <= 2
+                if (i == 0 && j == 0) {
+                    base = R[0];
+#pragma unroll
+                    for (int d = 0; d < D; ++d) bc[d] = R[Mo::O1 + d];
+                } else if (i == 0) {
+                    base = R[Mo::O1 + j - 1];
+#pragma unroll
+                    for (int d = 0; d < D; ++d) bc[d] = mono2<D>(R, j - 1, d);
+                } else {
+                    base = mono2<D>(R, i - 1, j - 1);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) bc[d] = mono3<D>(R, i - 1, j - 1, d);
+                }
+            } else if (i < M - 1) {                 // psi_i psi_E
+                if (i == 0) {
+                    base = 0.5 * (s2 + nb * R[0]);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) bc[d] = 0.5 * (s2c[d] + nb * R[Mo::O1 + d]);
+                } else {
+                    const int a = i - 1;
+                    base = 0.5 * (s2c[a] + nb * R[Mo::O1 + a]);
+#pragma unroll
+                    for (int d = 0; d < D; ++d)
+                        bc[d] = 0.5 * (R[Mo::OQ2 + (a <= d ? pair_index(D, a, d) : pair_index(D, d, a))] +
+                                       nb * mono2<D>(R, a, d));
+                }
+            } else {                                // psi_E^2
+                base = 0.25 * (R[Mo::OQ4] + 2.0 * nb * s2 + xb * R[0]);
+#pragma unroll
+                for (int d = 0; d < D; ++d) bc[d] = 0.25 * (R[Mo::OQ4 + 1 + d] + 2.0 * nb * s2c[d] + xb * R[Mo::O1 + d]);
+            }
+            S[t] = base;
+#pragma unroll
+            for (int d = 0; d < D; ++d) S[NS * (1 + d) + t] = bc[d];
+            ++t;
         }
 }
 
@@ -634,28 +715,44 @@ __global__ void k_face_sum2(DevCase<T> dc)
     if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
     const T *fr = dc.frec + (size_t)f * FREC;
     T U0[D];
+#pragma unroll
     for (int d = 0; d < D; ++d) U0[d] = fr[FR_U + d];
-    const T lam = fr[FR_LAM], pref = fr[FR_PREF], nb = fr[FR_NB], xb = fr[FR_XB], nl2 = fr[FR_NL2];
-    T acc[S2];
-    for (int i = 0; i < S2; ++i) acc[i] = 0;
+    const T lam = fr[FR_LAM], pref = fr[FR_PREF], nl2 = fr[FR_NL2];
+    using Mo = Mono<D>;
+    T r[Mo::N];
+#pragma unroll
+    for (int i = 0; i < Mo::N; ++i) r[i] = 0;
     for (int k = lane; k < dc.nvp; k += 32) {
         T c[D], c2 = 0;
+#pragma unroll
         for (int d = 0; d < D; ++d) {
             c[d] = dc.u[d][k] - U0[d];
             c2 += c[d] * c[d];
         }
-        const T wH = dc.w[k] * pref * gauss<T>(lam, nl2, c2);
-        T P[NS];
-        psi_c_outer<T, D>(c, c2, nb, xb, P);
-        for (int i = 0; i < NS; ++i) {
-            const T v = wH * P[i];
-            acc[i] += v;
-            for (int d = 0; d < D; ++d) acc[NS * (1 + d) + i] += c[d] * v;
+        const T a = dc.w[k] * pref * gauss<T>(lam, nl2, c2);
+        r[0] += a;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const T a1 = a * c[d];
+            r[Mo::O1 + d] += a1;
+#pragma unroll
+            for (int e = d; e < D; ++e) {
+                const T a2 = a1 * c[e];
+                r[Mo::O2 + pair_index(D, d, e)] += a2;
+                r[Mo::OQ2 + pair_index(D, d, e)] += a2 * c2;
+#pragma unroll
+                for (int g = e; g < D; ++g) r[Mo::O3 + triple_index(D, d, e, g)] += a2 * c[g];
+            }
         }
+        const T a4 = a * c2 * c2;
+        r[Mo::OQ4] += a4;
+#pragma unroll
+        for (int d = 0; d < D; ++d) r[Mo::OQ4 + 1 + d] += a4 * c[d];
     }
-    for (int i = 0; i < S2; ++i) {
-        T s = warp_sum(acc[i]);
-        if (lane == 0) dc.fsum2[(size_t)f * S2 + i] = (double)s;
+#pragma unroll
+    for (int i = 0; i < Mo::N; ++i) {
+        const T sm = warp_sum(r[i]);
+        if (lane == 0) dc.fsum2[(size_t)f * S2 + i] = (double)sm;
     }
 }
 
@@ -799,6 +896,10 @@ __global__ void k_face_fin2(DevCase<T> dc)
         const double lam0 = pq[D + 1];
         sep_moments<D>(m1, pref_of(pq[0], lam0, D), dc.nxi / (2.0 * lam0),
                        dc.nxi * (dc.nxi + 2.0) / (4.0 * lam0 * lam0), Ssep);
+        S = Ssep;
+    } else {
+        const double lam0 = dc.fprim0[(size_t)f * M + D + 1];
+        mono_moments<D>(S, dc.nxi / (2.0 * lam0), dc.nxi * (dc.nxi + 2.0) / (4.0 * lam0 * lam0), Ssep);
         S = Ssep;
     }
     double Mc[M * M], Tc[D][M * M];
