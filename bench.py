@@ -42,6 +42,33 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# FP32 ceiling: 152 SMs x 128 FP32 lanes x 2 flops per FMA at the 2070 MHz
+# maximum SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def _gather_flops_per_cvu(D, NC, nf):
+    """FP32 arithmetic of the gather pass per cell-velocity, counted from its
+    formulas (add, sub, mul 1 flop; FMA 2; exp2 and division 1): the limited
+    slope of the cell, the flux of each of its nf faces (the gather evaluates
+    every face of a cell, so an interior face twice over the mesh), stage 1 and
+    the residual moments.  Ring slopes, address arithmetic, compares and
+    selects are not counted."""
+    slope = NC * (nf * (1 + 2 * D)                 # differences and least-squares sums
+                  + nf * (2 * D + 10)              # Venkatakrishnan function at each face
+                  + 3 * D + 3)                     # foot point, positivity scaling
+    poly = D * D + 6 * D + 2                       # per-face polynomial of degree 3 in c
+    face = ((2 * D - 1)                            # u . n
+            + NC * (4 * D - 1)                     # upwind value and u . grad f
+            + D + (2 * D - 1) + 3                  # c, |c|^2, H0
+            + NC * (poly + 6)                      # flux of each component
+            + 2 * NC)                              # residual
+    stage1 = (D + 2 * (2 * D - 1) + 9 + (5 if NC == 2 else 0)   # Shakhov f+
+              + 4 * NC                                          # stage-1 update
+              + (2 * D - 1) + 2 + 2 * D + (5 if NC == 2 else 3))  # moments of the residual
+    return slope + nf * face + stage1
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -390,6 +417,10 @@ def main():
     alg_bytes = 2 * C * nc * Nv * 4
     achieved = alg_bytes / (g_ms * 1e-3) / 1e9 if g_ms > 0 else None
     share = {k: round(v / max(sum(groups.values()), 1e-12), 4) for k, v in groups.items()}
+    # the second ceiling: FP32 arithmetic of the gather against the FP32 peak
+    nf = float((np.asarray(case["mesh"]["face_cells"]) >= 0).sum()) / C
+    flops_cvu = _gather_flops_per_cvu(info["dim"], nc, nf)
+    alu_achieved = flops_cvu * C * Nv / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None
 
     # e2e: state in pinned host memory -> ugks_set_state_f32 -> ugks_step -> ugks_moments
     f_host_bytes = C * nc * Nv * 4
@@ -438,6 +469,10 @@ def main():
                                                 info["gather_threads"]),
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": g_ms, "group_share": share},
+        "alu_roofline": {"bound": "alu", "kernel": "k_gather", "achieved": alu_achieved, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": (alu_achieved / FP32_PEAK_TFLOPS) if alu_achieved else None,
+                         "flops_per_cvu": round(flops_cvu, 1), "faces_per_cell": round(nf, 3),
+                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "fp64_plain": {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": fp64_steps,
                        "speedup_of_fp32_form": value / v64},
         "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
