@@ -210,14 +210,15 @@ ugks_status ugks_profile_end(ugks_case *c, double *ms, int32_t n, int32_t *steps
 
 /* Batched stepping of several cases (one GPU).  The cases must share the
  * dimension and precision.  Each batch step runs every case's gather pass in
- * one persistent kernel per velocity-tile width present in the batch, which
- * walks a (case, patch, velocity tile) work list, and the other kernels of
- * every case on parallel graph
- * branches; the whole step is captured once as a CUDA graph on `stream`
- * (cudaStream_t, NULL: a stream of the batch's own) and replayed.  Results
- * are bit-identical to stepping each case alone with ugks_step.  The cases
- * stay owned by the caller and must outlive the batch; ugks_batch_step
- * advances each case's step counter. */
+ * one persistent kernel per (velocity-tile width, block size) present in the
+ * batch, which walks a (case, patch, velocity tile) work list, and each of the
+ * step's other kernels once for all cases (block offsets per case), so a
+ * step is about a dozen launches whatever the number of cases.  The whole
+ * step is captured once as a CUDA graph on `stream` (cudaStream_t, NULL: a
+ * stream of the batch's own) and replayed.  Results are bit-identical to
+ * stepping each case alone with ugks_step.  The cases stay owned by the
+ * caller and must outlive the batch; ugks_batch_step advances each case's
+ * step counter. */
 typedef struct ugks_batch ugks_batch;
 ugks_status ugks_batch_create(ugks_case *const *cases, int32_t n, void *stream, ugks_batch **out);
 ugks_status ugks_batch_step(ugks_batch *b, int32_t nsteps);
@@ -228,8 +229,8 @@ void ugks_batch_destroy(ugks_batch *b);
  * admits arrived requests, first fit in arrival order, while a slot is free
  * and the request's estimated device footprint (two copies of f plus the
  * O(cells + faces) arrays) fits the remaining budget; steps every running case
- * steps_per_tick times in batches (ugks_batch: one persistent gather launch per
- * step, CUDA-graph replay); then reads each running case's residual and retires
+ * steps_per_tick times in batches (ugks_batch: one launch per kernel of the step
+ * for all cases, CUDA-graph replay); then reads each running case's residual and retires
  * the converged ones (max_m r_m < tol), those at max_steps (status
  * UGKS_ENOTCONVERGED) and those with a numeric failure, keeping their rho, U,
  * T, q on the host and freeing their device memory.  The server is

@@ -1258,16 +1258,19 @@ struct ugks_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void *dcases = nullptr;         // device array of DevCase<T>
-    // one persistent gather launch per velocity tile present in the batch
+    // one persistent gather launch per (velocity tile, threads per CTA) in the batch
     struct Group {
         int vtile = 0, nth = 256, nwork = 0, grid = 0;
         int4 *work = nullptr;
         size_t smem = 0;
     };
     std::vector<Group> groups;
-    static constexpr int NB = 8;    // parallel branches for the per-case kernels
-    cudaStream_t br[NB] = {};
-    cudaEvent_t fork = nullptr, fork2 = nullptr, join[NB] = {}, join2[NB] = {};
+    // the other kernels of a step, one launch each over all cases: block offsets
+    // off[k][0..n] (device, prefix sums of the cases' block counts), total
+    // blocks and dynamic shared memory per kernel
+    int *small_off = nullptr;
+    int small_blocks[ugks::SK_COUNT] = {};
+    size_t small_smem[ugks::SK_COUNT] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaEvent_t> case_ev;   // orders each case's stream with the batch stream
@@ -1291,6 +1294,20 @@ void batch_build(ugks_batch *b)
     for (int i = 0; i < n; ++i) h[i] = dc_of<T>(b->cases[i]);
     cuda_ok(cudaMalloc(&b->dcases, sizeof(ugks::DevCase<T>) * n), "batch alloc");
     cuda_ok(cudaMemcpy(b->dcases, h.data(), sizeof(ugks::DevCase<T>) * n, cudaMemcpyHostToDevice), "batch upload");
+    // offsets of the batched per-case kernels
+    std::vector<int> off((size_t)ugks::SK_COUNT * (n + 1), 0);
+    for (int k = 0; k < ugks::SK_COUNT; ++k) {
+        int *o = &off[(size_t)k * (n + 1)];
+        for (int i = 0; i < n; ++i) {
+            const long long nb = (long long)o[i] + ugks::small_kernel_blocks<T>(h[i], k);
+            if (nb > INT32_MAX) fail(UGKS_EINVAL, "batch too large for one launch of kernel %d", k);
+            o[i + 1] = (int)nb;
+            b->small_smem[k] = std::max(b->small_smem[k], ugks::small_kernel_smem<T>(h[i], k));
+        }
+        b->small_blocks[k] = o[n];
+    }
+    cuda_ok(cudaMalloc((void **)&b->small_off, off.size() * sizeof(int)), "batch alloc");
+    cuda_ok(cudaMemcpy(b->small_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice), "batch upload");
     // one persistent launch per (velocity tile, threads per CTA) in the batch
     std::vector<std::pair<int, int>> tiles;
     for (auto *c : b->cases)
@@ -1328,29 +1345,21 @@ template <typename T>
 void batch_capture(ugks_batch *b)
 {
     cudaStream_t st = b->stream;
+    const int n = (int)b->cases.size();
+    const auto *dcs = (const ugks::DevCase<T> *)b->dcases;
+    auto small = [&](int k) {
+        cuda_ok(ugks::launch_small_batch<T>(b->D, k, dcs, b->small_off + (size_t)k * (n + 1), n, b->small_blocks[k],
+                                            b->small_smem[k], st),
+                "batched step kernel");
+    };
     cuda_ok(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
-    cuda_ok(cudaEventRecord(b->fork, st), "fork");
-    for (int k = 0; k < ugks_batch::NB; ++k) cuda_ok(cudaStreamWaitEvent(b->br[k], b->fork, 0), "fork wait");
-    for (size_t i = 0; i < b->cases.size(); ++i)
-        cuda_ok(ugks::launch_pre_gather(dc_of<T>(b->cases[i]), b->br[i % ugks_batch::NB]), "pre-gather");
-    for (int k = 0; k < ugks_batch::NB; ++k) {
-        cuda_ok(cudaEventRecord(b->join[k], b->br[k]), "join");
-        cuda_ok(cudaStreamWaitEvent(st, b->join[k], 0), "join wait");
-    }
+    for (int k = ugks::SK_PREP; k <= ugks::SK_WALL_SUM; ++k) small(k);
     for (const auto &g : b->groups)
         cuda_ok(ugks::launch_gather_batch<T>(b->D, g.vtile, g.nth, (const ugks::DevCase<T> *)b->dcases, g.work,
                                              g.nwork, g.grid, g.smem, st),
                 "batched gather");
-    cuda_ok(cudaEventRecord(b->fork2, st), "fork");
-    for (int k = 0; k < ugks_batch::NB; ++k) cuda_ok(cudaStreamWaitEvent(b->br[k], b->fork2, 0), "fork wait");
-    for (size_t i = 0; i < b->cases.size(); ++i) {
-        ugks_case *c = b->cases[i];
-        cuda_ok(ugks::launch_post_gather(dc_of<T>(c), c->cfg, b->br[i % ugks_batch::NB]), "post-gather");
-    }
-    for (int k = 0; k < ugks_batch::NB; ++k) {
-        cuda_ok(cudaEventRecord(b->join2[k], b->br[k]), "join");
-        cuda_ok(cudaStreamWaitEvent(st, b->join2[k], 0), "join wait");
-    }
+    small(ugks::SK_UPDATE_W);
+    small(ugks::SK_COLLIDE);
     cuda_ok(cudaStreamEndCapture(st, &b->graph), "end capture");
     cuda_ok(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
 }
@@ -1363,13 +1372,7 @@ void batch_free(ugks_batch *b)
     if (b->dcases) cudaFree(b->dcases);
     for (auto &g : b->groups)
         if (g.work) cudaFree(g.work);
-    for (int k = 0; k < ugks_batch::NB; ++k) {
-        if (b->br[k]) cudaStreamDestroy(b->br[k]);
-        if (b->join[k]) cudaEventDestroy(b->join[k]);
-        if (b->join2[k]) cudaEventDestroy(b->join2[k]);
-    }
-    if (b->fork) cudaEventDestroy(b->fork);
-    if (b->fork2) cudaEventDestroy(b->fork2);
+    if (b->small_off) cudaFree(b->small_off);
     for (auto e : b->case_ev)
         if (e) cudaEventDestroy(e);
     if (b->done) cudaEventDestroy(b->done);
@@ -1406,13 +1409,6 @@ ugks_status ugks_batch_create(ugks_case *const *cases, int32_t n, void *stream, 
             cuda_ok(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "stream");
             b->own_stream = true;
         }
-        for (int k = 0; k < ugks_batch::NB; ++k) {
-            cuda_ok(cudaStreamCreateWithFlags(&b->br[k], cudaStreamNonBlocking), "stream");
-            cuda_ok(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming), "event");
-            cuda_ok(cudaEventCreateWithFlags(&b->join2[k], cudaEventDisableTiming), "event");
-        }
-        cuda_ok(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
-        cuda_ok(cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming), "event");
         cuda_ok(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming), "event");
         b->case_ev.assign(b->cases.size(), nullptr);
         for (auto &e : b->case_ev) cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");

@@ -113,6 +113,36 @@ __device__ __forceinline__ double venkat_d(double d1, double d2, double e2)
     return den > 0.0 ? num / den : 1.0;
 }
 
+// ------------------------------------------------------------ batched launches
+// The per-case kernels of a step (all but the gather) are written as bodies of
+// a block index.  k_X runs them for one case (block index = blockIdx.x);
+// k_X_batch runs them for many cases of a batch in one launch.  Its block b
+// belongs to the last case i with off[i] <= b (off[] holds the prefix sums of
+// the cases' block counts, so a case without blocks is never chosen) and runs
+// that case's local block b - off[i]: the same arithmetic as the single-case
+// launch.  The case's DevCase is copied into shared memory, where its fields
+// are read without aliasing the arrays the kernel writes.
+template <typename T>
+__device__ __forceinline__ const DevCase<T> &batch_case(const DevCase<T> *__restrict__ cases,
+                                                       const int *__restrict__ off, int n, int &bx)
+{
+    __shared__ __align__(16) unsigned char raw[sizeof(DevCase<T>)];
+    static_assert(sizeof(DevCase<T>) % sizeof(int) == 0, "DevCase is copied in 4-byte words");
+    const int b = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    bx = b - __ldg(off + lo);
+    const int *src = reinterpret_cast<const int *>(cases + lo);
+    int *dst = reinterpret_cast<int *>(raw);
+    for (int w = threadIdx.x; w < (int)(sizeof(DevCase<T>) / sizeof(int)); w += blockDim.x) dst[w] = __ldg(src + w);
+    __syncthreads();
+    return *reinterpret_cast<const DevCase<T> *>(raw);
+}
+
 // ------------------------------------------------------------ init / moments
 template <typename T, int D, int NC>
 __global__ void k_init_f(DevCase<T> dc)
@@ -167,9 +197,9 @@ __global__ void k_heatflux(DevCase<T> dc)
 
 // ------------------------------------------------------------ k_prep
 template <typename T, int D, int NC>
-__global__ void k_prep(DevCase<T> dc)
+__device__ __forceinline__ void prep_body(const DevCase<T> &dc, const int bx)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = bx * blockDim.x + threadIdx.x;
     constexpr int M = D + 2;
     if (t < dc.C) {
         const int c = t;
@@ -215,13 +245,27 @@ __global__ void k_prep(DevCase<T> dc)
     r[GR_NL2] = (T)(-p.lam * LOG2E);
 }
 
+template <typename T, int D, int NC>
+__global__ void k_prep(DevCase<T> dc)
+{
+    prep_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void k_prep_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    prep_body<T, D, NC>(dc, bx);
+}
+
 // ------------------------------------------------------------ k_macro_grad
 // limited least-squares gradients of the primitive variables (rho, U, T) and
 // the conserved-variable gradient obtained from them by the chain rule
 template <typename T, int D, int NC>
-__global__ void k_macro_grad(DevCase<T> dc)
+__device__ __forceinline__ void macro_grad_body(const DevCase<T> &dc, const int bx)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = bx * blockDim.x + threadIdx.x;
     constexpr int M = D + 2;
     if (c >= dc.C) return;
     const double *Pc = dc.prim + (size_t)c * M;
@@ -267,6 +311,20 @@ __global__ void k_macro_grad(DevCase<T> dc)
         }
         gw[D + 1] = gp[d][0] * (0.5 * uu + 1.5 * Pc[D + 1]) + Pc[0] * (udu + 1.5 * gp[d][D + 1]);
     }
+}
+
+template <typename T, int D, int NC>
+__global__ void k_macro_grad(DevCase<T> dc)
+{
+    macro_grad_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void k_macro_grad_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    macro_grad_body<T, D, NC>(dc, bx);
 }
 
 // ------------------------------------------------------------ face pass
@@ -333,9 +391,9 @@ __device__ void add_half_range(const Prim &p, const double n[D], double sigma, d
 }
 
 template <typename T, int D, int NC>
-__global__ void k_face_pre(DevCase<T> dc)
+__device__ __forceinline__ void face_pre_body(const DevCase<T> &dc, const int bx)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = bx * blockDim.x + threadIdx.x;
     constexpr int M = D + 2;
     if (f >= dc.F) return;
     const int typ = dc.ftype[f];
@@ -388,11 +446,25 @@ __global__ void k_face_pre(DevCase<T> dc)
     }
 }
 
+template <typename T, int D, int NC>
+__global__ void k_face_pre(DevCase<T> dc)
+{
+    face_pre_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_pre_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    face_pre_body<T, D, NC>(dc, bx);
+}
+
 // half-range moments: sum_k w psi_c [H(u_n) g_L + (1 - H(u_n)) g_R], centred at U_ref
 template <typename T, int D, int NC>
-__global__ void k_face_sum1(DevCase<T> dc)
+__device__ __forceinline__ void face_sum1_body(const DevCase<T> &dc, const int bx)
 {
-    const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int f = bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     constexpr int M = D + 2;
     if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
@@ -435,6 +507,20 @@ __global__ void k_face_sum1(DevCase<T> dc)
     }
 }
 
+template <typename T, int D, int NC>
+__global__ void k_face_sum1(DevCase<T> dc)
+{
+    face_sum1_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_sum1_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    face_sum1_body<T, D, NC>(dc, bx);
+}
+
 // k_face_sum1 on a tensor-product velocity grid.  With the face-state
 // Maxwellians factored by axis, the half-range sums become, for every point of
 // the outer axes, sums over a contiguous range of the last axis: u.n, rounded
@@ -447,12 +533,12 @@ __global__ void k_face_sum1(DevCase<T> dc)
 constexpr int SUM1_SEP_WARPS = 4;
 
 template <typename T, int D, int NC>
-__global__ void __launch_bounds__(32 * SUM1_SEP_WARPS) k_face_sum1_sep(DevCase<T> dc)
+__device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const int bx)
 {
     extern __shared__ __align__(16) unsigned char psum_raw[];
     T *psum = reinterpret_cast<T *>(psum_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int f = blockIdx.x * SUM1_SEP_WARPS + warp;
+    const int f = bx * SUM1_SEP_WARPS + warp;
     constexpr int M = D + 2;
     constexpr int L = D - 1;                 // the prefix-sum axis
     const int NL = dc.cart_n[L];
@@ -564,9 +650,23 @@ __global__ void __launch_bounds__(32 * SUM1_SEP_WARPS) k_face_sum1_sep(DevCase<T
 }
 
 template <typename T, int D, int NC>
-__global__ void k_face_fin1(DevCase<T> dc)
+__global__ void __launch_bounds__(32 * SUM1_SEP_WARPS) k_face_sum1_sep(DevCase<T> dc)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    face_sum1_sep_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void __launch_bounds__(32 * SUM1_SEP_WARPS) k_face_sum1_sep_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    face_sum1_sep_body<T, D, NC>(dc, bx);
+}
+
+template <typename T, int D, int NC>
+__device__ __forceinline__ void face_fin1_body(const DevCase<T> &dc, const int bx)
+{
+    const int f = bx * blockDim.x + threadIdx.x;
     constexpr int M = D + 2;
     if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
     const double *S = dc.fsum1 + (size_t)f * M;
@@ -598,6 +698,20 @@ __global__ void k_face_fin1(DevCase<T> dc)
     r[FR_NB] = (T)(dc.nxi / (2.0 * p.lam));
     r[FR_XB] = (T)(dc.nxi * (dc.nxi + 2.0) / (4.0 * p.lam * p.lam));
     r[FR_NL2] = (T)(-p.lam * LOG2E);
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_fin1(DevCase<T> dc)
+{
+    face_fin1_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_fin1_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    face_fin1_body<T, D, NC>(dc, bx);
 }
 
 // number of unique entries of a symmetric (D+2)x(D+2) matrix
@@ -706,9 +820,9 @@ __device__ void mono_moments(const double *R, double nb, double xb, double *S)
 }
 
 template <typename T, int D, int NC>
-__global__ void k_face_sum2(DevCase<T> dc)
+__device__ __forceinline__ void face_sum2_body(const DevCase<T> &dc, const int bx)
 {
-    const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int f = bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     constexpr int NS = Sym<D>::N;
     constexpr int S2 = NS * (D + 1);
@@ -756,6 +870,20 @@ __global__ void k_face_sum2(DevCase<T> dc)
     }
 }
 
+template <typename T, int D, int NC>
+__global__ void k_face_sum2(DevCase<T> dc)
+{
+    face_sum2_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_sum2_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    face_sum2_body<T, D, NC>(dc, bx);
+}
+
 // The same sums as k_face_sum2 on a tensor-product velocity grid, where
 // u_k = (x_i, y_j[, z_l]) and w_k = wx_i wy_j [wz_l]: every moment of g0 the slope
 // systems need is sum_k w_k H0(u_k) c^alpha = pref0 prod_d m_d[alpha_d] with the
@@ -763,9 +891,9 @@ __global__ void k_face_sum2(DevCase<T> dc)
 // This kernel reduces the 1-D moments (warp per face); k_face_fin2 forms the
 // products (thread per face, FP64).
 template <typename T, int D, int NC>
-__global__ void k_face_sum2_sep(DevCase<T> dc)
+__device__ __forceinline__ void face_sum2_sep_body(const DevCase<T> &dc, const int bx)
 {
-    const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int f = bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     constexpr int NS = Sym<D>::N;
     if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
@@ -790,6 +918,20 @@ __global__ void k_face_sum2_sep(DevCase<T> dc)
             if (lane == pw) out[d * 6 + pw] = (double)sm;
         }
     }
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_sum2_sep(DevCase<T> dc)
+{
+    face_sum2_sep_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_sum2_sep_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    face_sum2_sep_body<T, D, NC>(dc, bx);
 }
 
 // M_c and T_c,d of k_face_sum2 from the 1-D moments m[d][0..5] (tensor grids)
@@ -881,9 +1023,9 @@ __device__ void chol_solve(int n, double *A, double *b, int nrhs, int ldb)
 // Mc beta_d = L^{-1} dW0/dx_d, and the compatibility condition gives
 // beta_A = L^T A = -Mc^{-1} sum_d Tc_d beta_d - sum_d U0_d beta_d.
 template <typename T, int D, int NC>
-__global__ void k_face_fin2(DevCase<T> dc)
+__device__ __forceinline__ void face_fin2_body(const DevCase<T> &dc, const int bx)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = bx * blockDim.x + threadIdx.x;
     constexpr int M = D + 2, NS = Sym<D>::N, S2 = NS * (D + 1);
     if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
     double Ssep[S2];
@@ -1016,17 +1158,31 @@ __global__ void k_face_fin2(DevCase<T> dc)
     }
 }
 
+template <typename T, int D, int NC>
+__global__ void k_face_fin2(DevCase<T> dc)
+{
+    face_fin2_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void k_face_fin2_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    face_fin2_body<T, D, NC>(dc, bx);
+}
+
 // ------------------------------------------------------------ walls
 // rho_w from zero net mass flux (Eq. maxWalldes): outgoing particles (u_n > 0)
 // carry the interior reconstruction transported freely over the step,
 // incoming ones the wall Maxwellian.
 template <typename T, int D, int NC>
-__global__ void __launch_bounds__(256) k_wall_sum(DevCase<T> dc)
+__device__ __forceinline__ void wall_sum_body(const DevCase<T> &dc, const int bx)
 {
     constexpr int M = D + 2;
     constexpr int NR = 2 + 2 * M;               // num, den, outgoing moments A, incoming moments B
     __shared__ T red[NR][8];
-    const int s = blockIdx.x;
+    const int s = bx;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (s >= dc.NW) return;
     const int f = dc.wface[s];
@@ -1120,6 +1276,20 @@ __global__ void __launch_bounds__(256) k_wall_sum(DevCase<T> dc)
         w[GR_PREF] = (T)pref_of(rw, lw, D);
         for (int m = 0; m < M; ++m) dc.wall_F[(size_t)s * M + m] = a[2 + m] + rw * a[2 + M + m];
     }
+}
+
+template <typename T, int D, int NC>
+__global__ void __launch_bounds__(256) k_wall_sum(DevCase<T> dc)
+{
+    wall_sum_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void __launch_bounds__(256) k_wall_sum_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    wall_sum_body<T, D, NC>(dc, bx);
 }
 
 // ------------------------------------------------------------ gather pass
@@ -1359,11 +1529,11 @@ __global__ void __launch_bounds__(NTH, NTH >= 512 ? 2 : 0) k_gather_batch(const 
 
 // ------------------------------------------------------------ W update
 template <typename T, int D, int NC>
-__global__ void __launch_bounds__(256) k_update_W(DevCase<T> dc)
+__device__ __forceinline__ void update_W_body(const DevCase<T> &dc, const int bx)
 {
     constexpr int M = D + 2;
     __shared__ double red[2 * M][8];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = bx * blockDim.x + threadIdx.x;
     double dsq[M], wsq[M];
     for (int m = 0; m < M; ++m) dsq[m] = wsq[m] = 0.0;
     if (c < dc.C) {
@@ -1401,8 +1571,22 @@ __global__ void __launch_bounds__(256) k_update_W(DevCase<T> dc)
     if (threadIdx.x < 2 * M) {
         double s = 0.0;
         for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
-        dc.res_part[(size_t)blockIdx.x * 2 * M + threadIdx.x] = s;
+        dc.res_part[(size_t)bx * 2 * M + threadIdx.x] = s;
     }
+}
+
+template <typename T, int D, int NC>
+__global__ void __launch_bounds__(256) k_update_W(DevCase<T> dc)
+{
+    update_W_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void __launch_bounds__(256) k_update_W_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    update_W_body<T, D, NC>(dc, bx);
 }
 
 template <int M>
@@ -1434,10 +1618,10 @@ template <> struct Vec4<double> { using type = double4_32a; };
 // 4 consecutive velocities per lane (rows are padded to a multiple of 32, so
 // every row start is 16-byte aligned for FP32 and 32-byte aligned for FP64)
 template <typename T, int D, int NC>
-__global__ void k_collide(DevCase<T> dc)
+__device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx)
 {
     using V4 = typename Vec4<T>::type;
-    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int c = bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (c >= dc.C) return;
     const T *kr = dc.krec + (size_t)c * CREC;
@@ -1490,6 +1674,20 @@ __global__ void k_collide(DevCase<T> dc)
         T s = warp_sum(acc[d]);
         if (lane == 0) dc.q[(size_t)c * D + d] = 0.5 * (double)s;
     }
+}
+
+template <typename T, int D, int NC>
+__global__ void k_collide(DevCase<T> dc)
+{
+    collide_body<T, D, NC>(dc, blockIdx.x);
+}
+
+template <typename T, int D, int NC>
+__global__ void k_collide_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+{
+    int bx;
+    const DevCase<T> &dc = batch_case(cases, off, n, bx);
+    collide_body<T, D, NC>(dc, bx);
 }
 
 // ------------------------------------------------------------ state I/O
@@ -1599,49 +1797,110 @@ static cudaError_t gather_dispatch(const DevCase<T> &dc, size_t smem, cudaStream
     return cudaErrorInvalidValue;
 }
 
+// Blocks, threads and dynamic shared memory of the per-case kernels of a step
+// (SmallKernel order); 0 blocks: the case does not run that kernel.
+template <typename T, int D>
+static int sk_blocks(const DevCase<T> &dc, int k)
+{
+    const int C = dc.C, F = dc.F;
+    const bool faces = F > 0, sums1 = faces && !dc.w0_analytic;
+    switch (k) {
+    case SK_PREP: return cdiv(C + dc.G, 128);
+    case SK_MACRO_GRAD: return cdiv(C, 128);
+    case SK_FACE_PRE: return faces ? cdiv(F, 128) : 0;
+    case SK_FACE_SUM1_SEP: return sums1 && dc.sep1 ? cdiv(F, SUM1_SEP_WARPS) : 0;
+    case SK_FACE_SUM1: return sums1 && !dc.sep1 ? cdiv(F, 8) : 0;
+    case SK_FACE_FIN1: return faces ? cdiv(F, 128) : 0;
+    case SK_FACE_SUM2_SEP: return faces && dc.sep ? cdiv(F, 8) : 0;
+    case SK_FACE_SUM2: return faces && !dc.sep ? cdiv(F, 8) : 0;
+    case SK_FACE_FIN2: return faces ? cdiv(F, 64) : 0;
+    case SK_WALL_SUM: return dc.NW;
+    case SK_UPDATE_W: return cdiv(C, 256);
+    case SK_COLLIDE: return cdiv(C, 8);
+    default: return 0;
+    }
+}
+
+constexpr int kSkThreads[SK_COUNT] = {128, 128, 128, 32 * SUM1_SEP_WARPS, 256, 128, 256, 256, 64, 256, 256, 256};
+
+template <typename T, int D>
+static size_t sk_smem(const DevCase<T> &dc, int k)
+{
+    // k_face_sum1_sep: prefix sums of the last axis, 2 sides x 3 powers per warp
+    return k == SK_FACE_SUM1_SEP ? (size_t)SUM1_SEP_WARPS * 6 * (dc.cart_n[D - 1] + 1) * sizeof(T) : 0;
+}
+
+// one per-case kernel, for one case (cases == nullptr) or for the cases of a
+// batch (block offsets off[0..n])
+template <typename T, int D, int NC>
+static cudaError_t sk_launch(int k, int blocks, size_t smem, cudaStream_t st, const DevCase<T> *dc,
+                             const DevCase<T> *cases, const int *off, int n)
+{
+    if (blocks <= 0) return cudaSuccess;
+    const int nt = kSkThreads[k];
+#define UGKS_SK(ID, K)                                                                                  \
+    case ID:                                                                                            \
+        if (cases) K##_batch<T, D, NC><<<blocks, nt, smem, st>>>(cases, off, n);                        \
+        else K<T, D, NC><<<blocks, nt, smem, st>>>(*dc);                                                \
+        break;
+    if (k == SK_FACE_SUM1_SEP && smem > 48 * 1024) {
+        cudaError_t e = cases ? cudaFuncSetAttribute(k_face_sum1_sep_batch<T, D, NC>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                              : cudaFuncSetAttribute(k_face_sum1_sep<T, D, NC>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    switch (k) {
+        UGKS_SK(SK_PREP, k_prep)
+        UGKS_SK(SK_MACRO_GRAD, k_macro_grad)
+        UGKS_SK(SK_FACE_PRE, k_face_pre)
+        UGKS_SK(SK_FACE_SUM1_SEP, k_face_sum1_sep)
+        UGKS_SK(SK_FACE_SUM1, k_face_sum1)
+        UGKS_SK(SK_FACE_FIN1, k_face_fin1)
+        UGKS_SK(SK_FACE_SUM2_SEP, k_face_sum2_sep)
+        UGKS_SK(SK_FACE_SUM2, k_face_sum2)
+        UGKS_SK(SK_FACE_FIN2, k_face_fin2)
+        UGKS_SK(SK_WALL_SUM, k_wall_sum)
+        UGKS_SK(SK_UPDATE_W, k_update_W)
+        UGKS_SK(SK_COLLIDE, k_collide)
+    default: return cudaErrorInvalidValue;
+    }
+#undef UGKS_SK
+    return cudaGetLastError();
+}
+
+template <typename T, int D, int NC>
+static void sk_case(const DevCase<T> &dc, int k, cudaStream_t st)
+{
+    sk_launch<T, D, NC>(k, sk_blocks<T, D>(dc, k), sk_smem<T, D>(dc, k), st, &dc, nullptr, nullptr, 0);
+}
+
 template <typename T, int D, int NC>
 static void pre_gather(const DevCase<T> &dc, cudaStream_t st, cudaEvent_t *ev)
 {
-    const int C = dc.C, F = dc.F;
     auto mark = [&](int i) {
         if (ev) cudaEventRecord(ev[i], st);
     };
     mark(0);
-    k_prep<T, D, NC><<<cdiv(C + dc.G, 128), 128, 0, st>>>(dc);
-    k_macro_grad<T, D, NC><<<cdiv(C, 128), 128, 0, st>>>(dc);
+    sk_case<T, D, NC>(dc, SK_PREP, st);
+    sk_case<T, D, NC>(dc, SK_MACRO_GRAD, st);
     mark(1);
-    if (F > 0) {
-        k_face_pre<T, D, NC><<<cdiv(F, 128), 128, 0, st>>>(dc);
-        if (dc.w0_analytic) {
-            // W0 came from k_face_pre
-        } else if (dc.sep1) {
-            const size_t sm = (size_t)SUM1_SEP_WARPS * 6 * (dc.cart_n[D - 1] + 1) * sizeof(T);
-            if (sm > 48 * 1024)
-                cudaFuncSetAttribute(k_face_sum1_sep<T, D, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_face_sum1_sep<T, D, NC><<<cdiv(F, SUM1_SEP_WARPS), 32 * SUM1_SEP_WARPS, sm, st>>>(dc);
-        } else {
-            k_face_sum1<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
-        }
-        k_face_fin1<T, D, NC><<<cdiv(F, 128), 128, 0, st>>>(dc);
-        if (dc.sep) k_face_sum2_sep<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
-        else k_face_sum2<T, D, NC><<<cdiv(F, 8), 256, 0, st>>>(dc);
-        k_face_fin2<T, D, NC><<<cdiv(F, 64), 64, 0, st>>>(dc);
-    }
+    for (int k = SK_FACE_PRE; k <= SK_FACE_FIN2; ++k) sk_case<T, D, NC>(dc, k, st);
     mark(2);
-    if (dc.NW > 0) k_wall_sum<T, D, NC><<<dc.NW, 256, 0, st>>>(dc);
+    sk_case<T, D, NC>(dc, SK_WALL_SUM, st);
     mark(3);
 }
 
 template <typename T, int D, int NC>
-static void post_gather(const DevCase<T> &dc, const StepConfig &cfg, cudaStream_t st, cudaEvent_t *ev)
+static void post_gather(const DevCase<T> &dc, const StepConfig &, cudaStream_t st, cudaEvent_t *ev)
 {
     auto mark = [&](int i) {
         if (ev) cudaEventRecord(ev[i], st);
     };
     mark(4);
-    k_update_W<T, D, NC><<<cfg.n_res_blocks, 256, 0, st>>>(dc);
+    sk_case<T, D, NC>(dc, SK_UPDATE_W, st);
     mark(5);
-    k_collide<T, D, NC><<<cdiv(dc.C, 8), 256, 0, st>>>(dc);
+    sk_case<T, D, NC>(dc, SK_COLLIDE, st);
     mark(6);
 }
 
@@ -1669,6 +1928,26 @@ cudaError_t launch_post_gather(const DevCase<T> &dc, const StepConfig &cfg, cuda
     if (dc.D == 2) post_gather<T, 2, 2>(dc, cfg, st, nullptr);
     else post_gather<T, 3, 1>(dc, cfg, st, nullptr);
     return cudaGetLastError();
+}
+
+template <typename T>
+int small_kernel_blocks(const DevCase<T> &dc, int k)
+{
+    return dc.D == 2 ? sk_blocks<T, 2>(dc, k) : sk_blocks<T, 3>(dc, k);
+}
+
+template <typename T>
+size_t small_kernel_smem(const DevCase<T> &dc, int k)
+{
+    return dc.D == 2 ? sk_smem<T, 2>(dc, k) : sk_smem<T, 3>(dc, k);
+}
+
+template <typename T>
+cudaError_t launch_small_batch(int D, int k, const DevCase<T> *cases, const int *off, int n, int blocks, size_t smem,
+                               cudaStream_t st)
+{
+    if (D == 2) return sk_launch<T, 2, 2>(k, blocks, smem, st, nullptr, cases, off, n);
+    return sk_launch<T, 3, 1>(k, blocks, smem, st, nullptr, cases, off, n);
 }
 
 template <typename T>
@@ -1827,6 +2106,14 @@ template cudaError_t launch_pre_gather<double>(const DevCase<double> &, cudaStre
 template cudaError_t launch_pre_gather<float>(const DevCase<float> &, cudaStream_t);
 template cudaError_t launch_post_gather<double>(const DevCase<double> &, const StepConfig &, cudaStream_t);
 template cudaError_t launch_post_gather<float>(const DevCase<float> &, const StepConfig &, cudaStream_t);
+template int small_kernel_blocks<double>(const DevCase<double> &, int);
+template int small_kernel_blocks<float>(const DevCase<float> &, int);
+template size_t small_kernel_smem<double>(const DevCase<double> &, int);
+template size_t small_kernel_smem<float>(const DevCase<float> &, int);
+template cudaError_t launch_small_batch<double>(int, int, const DevCase<double> *, const int *, int, int, size_t,
+                                                cudaStream_t);
+template cudaError_t launch_small_batch<float>(int, int, const DevCase<float> *, const int *, int, int, size_t,
+                                               cudaStream_t);
 template cudaError_t launch_gather<double>(const DevCase<double> &, size_t, cudaStream_t);
 template cudaError_t launch_gather<float>(const DevCase<float> &, size_t, cudaStream_t);
 template cudaError_t launch_gather_batch<double>(int, int, int, const DevCase<double> *, const int4 *, int, int, size_t,

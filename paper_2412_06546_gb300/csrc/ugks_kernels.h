@@ -26,6 +26,20 @@ template <typename T>
 cudaError_t launch_gather_batch(int D, int vtile, int nth, const DevCase<T> *cases, const int4 *work, int nwork,
                                 int grid, size_t smem, cudaStream_t st);
 template <typename T> int gather_resident_ctas(int D, int vtile, int nth, size_t smem);
+// The per-case kernels of a step, in launch order: pre-gather (SK_PREP ..
+// SK_WALL_SUM), then after the gather SK_UPDATE_W and SK_COLLIDE.
+enum SmallKernel {
+    SK_PREP, SK_MACRO_GRAD, SK_FACE_PRE, SK_FACE_SUM1_SEP, SK_FACE_SUM1, SK_FACE_FIN1,
+    SK_FACE_SUM2_SEP, SK_FACE_SUM2, SK_FACE_FIN2, SK_WALL_SUM, SK_UPDATE_W, SK_COLLIDE, SK_COUNT
+};
+// blocks (0: not run) and dynamic shared memory of kernel k for a case (a host copy of its DevCase)
+template <typename T> int small_kernel_blocks(const DevCase<T> &dc, int k);
+template <typename T> size_t small_kernel_smem(const DevCase<T> &dc, int k);
+// kernel k over n cases in one launch: cases[] a device array of their DevCase,
+// off[0..n] the device prefix sums of their block counts, blocks = off[n]
+template <typename T>
+cudaError_t launch_small_batch(int D, int k, const DevCase<T> *cases, const int *off, int n, int blocks, size_t smem,
+                               cudaStream_t st);
 template <typename T> cudaError_t launch_heatflux(const DevCase<T> &dc, cudaStream_t st);
 // state I/O between the internal layout and a host-layout staging buffer of
 // element type S (double or float)

@@ -5,8 +5,9 @@
 //   1. admits arrived requests, first fit in arrival order, while a slot is
 //      free and the request's device footprint fits the remaining budget;
 //   2. steps all running cases together: cases are grouped by (dimension,
-//      precision, velocity tile) into ugks_batch objects (one persistent gather
-//      launch per step, CUDA-graph replay), rebuilt when the running set changes;
+//      precision) into ugks_batch objects (each kernel of a step launched once
+//      for all cases of a group, CUDA-graph replay), rebuilt when the running
+//      set changes;
 //   3. reads every running case's residual and retires the converged ones
 //      (max_m r_m < tol), those at their step limit and those with a numeric
 //      failure, copying their macroscopic fields to host memory and freeing

@@ -90,3 +90,44 @@ def test_batch_rejects_mixed_precision():
     with pytest.raises(_lib.UGKSError) as e:
         _lib.Batch([g1, g2])
     assert e.value.code == 1
+
+
+def _variant_cases():
+    """2D cases that take different kernels of a step: separable face sums
+    (tensor grid, walls), general face sums (unstructured velocity set),
+    the analytic W0 (no first face reduction) and a periodic mesh (no walls,
+    no far field)."""
+    rng = np.random.default_rng(8)
+    cav = cs.cavity_case(n=9, nv=14, Kn=0.2, lid=0.4)
+    cyl = cs.cylinder_case(n_cells=700, nvx=12, nvy=12, mach=2.0)
+    vg = cyl["vgrid"]
+    perm = rng.permutation(len(vg["w"]))
+    u = np.asarray(vg["u"])[perm] + rng.uniform(-0.1, 0.1, size=np.asarray(vg["u"]).shape)
+    w = np.asarray(vg["w"])[perm] * rng.uniform(0.9, 1.1, size=len(perm))
+    unstructured = dict(cyl, vgrid={"dim": 2, "u": u, "w": w, "cart_n": [0, 0, 0]})
+    analytic = cs.cylinder_case(n_cells=500, nvx=10, nvy=11, mach=1.2, Kn=0.5)
+    analytic = dict(analytic, params=dict(analytic["params"], w0_analytic=1))
+    mesh = cs.periodic_tri_mesh(7, 6, 1.0, 0.8, jitter=0.2, seed=4)
+    periodic = {"mesh": mesh, "vgrid": cs.cartesian_vgrid((10, 9), (-5, -4.5), (5, 4.5)),
+                "params": cs.params(0.05), "init": cs.smooth_state(mesh, 5, 0.15, U0=[0.3, -0.2])}
+    return [cav, unstructured, analytic, periodic]
+
+
+@pytest.mark.parametrize("precision", [_lib.FP32, _lib.FP64])
+def test_batch_with_cases_that_skip_kernels(precision):
+    """Every kernel of a batch step is one launch over all cases; a case that
+    does not run a kernel (no walls, no general sums, no first reduction)
+    owns no blocks of it.  Each case still matches itself stepped alone."""
+    specs = _variant_cases()
+    mk = lambda c: _lib.Case(c["mesh"], c["vgrid"], c["params"], c["init"], precision=precision)
+    alone = [mk(c) for c in specs]
+    for g in alone:
+        g.step(3)
+    together = [mk(c) for c in specs]
+    b = _lib.Batch(together)
+    b.step(3)
+    for a, t in zip(alone, together):
+        assert np.array_equal(a.state()[0], t.state()[0])
+        assert np.array_equal(a.state()[1], t.state()[1])
+        assert np.array_equal(a.residual(), t.residual())
+    b.close()
