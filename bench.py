@@ -139,6 +139,8 @@ def _workload(name):
         return cases.cavity_case()
     if name == "sphere_Ma4_Kn0.1_tet150k_v28":
         return cases.sphere_case()
+    if name == "sphere_Ma4_Kn0.1_tet20k_v28":           # the same flow on 20k cells (profiling captures)
+        return cases.sphere_case(n_cells=20000)
     if name == "x38_Ma8_Kn0.005_tet1.05M_v4548":
         return cases.x38_case()
     raise SystemExit(f"unknown workload {name}")
@@ -188,7 +190,7 @@ def _gather_sources():
         return k[a:b] + fh.read()
 
 
-def _gather_traffic(workload, patch, vtile, threads):
+def _gather_traffic(workload, patch, vtile, threads, group):
     """DRAM bytes of one gather launch from the committed ncu summary, while
     the gather's sources and tiling are those the counters were taken on
     (else None: the kernel changed since)."""
@@ -206,7 +208,7 @@ def _gather_traffic(workload, patch, vtile, threads):
             fields[k] = v.strip()
     if fields.get("gather-sources-sha256-16") != h.hexdigest()[:16]:
         return None
-    if fields.get("traffic-tiling") != f"patch {patch}, vtile {vtile}, threads {threads}":
+    if fields.get("traffic-tiling") != f"patch {patch}, vtile {vtile}, threads {threads}, group {group}":
         return None
     return int(fields["traffic-bytes-per-launch"])
 
@@ -360,6 +362,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=0, help="steps of the FP64 plain path (0: steps/10)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 leg")
     ap.add_argument("--ref-steps", type=int, default=0)
     ap.add_argument("--ref-warmup", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -374,6 +377,8 @@ def main():
     ap.add_argument("--patch", type=int, default=0)
     ap.add_argument("--vtile", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="gather CTA size, 256 or 512 (0: autotuned)")
+    ap.add_argument("--tile-group", type=int, default=0,
+                    help="velocity tiles per group of the gather grid order (0: autotuned)")
     ap.add_argument("--w0-analytic", action="store_true",
                     help="interface W0 from the analytic half-range moments (the variant of the N4 row)")
     args = ap.parse_args()
@@ -401,7 +406,7 @@ def main():
     with torch.cuda.stream(stream):
         g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32,
                       stream=stream.cuda_stream, patch_cells=args.patch, vtile=args.vtile,
-                      threads=args.threads)
+                      threads=args.threads, tile_group=args.tile_group)
     info = g.info()
     C, Nv, nc = info["n_cells"], info["nv"], info["ncomp"]
     ms, groups, clocks = _time_steps(torch, g, args.steps, args.warmup, dist, local)
@@ -435,15 +440,19 @@ def main():
     # the plain FP64 path on the same case (fixed tiling on large cases, where
     # the autotuner's trial launches would take minutes)
     fp64_steps = args.fp64_steps or max(3, args.steps // 10)
-    tiling = {"patch_cells": 16, "vtile": 32} if C * Nv > LARGE_CVU else {}
-    with torch.cuda.stream(stream):
-        g64 = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP64,
-                        stream=stream.cuda_stream, **tiling)
-    ms64, groups64, _ = _time_steps(torch, g64, fp64_steps, 2, dist, local)
-    g64.check()
-    ms64 = _max_over_ranks(torch, dist, ms64) / fp64_steps
-    v64 = ws * C * Nv / (ms64 * 1e-3)
-    g64.close()
+    fp64 = {"skipped": "not requested"}
+    if not args.no_fp64:
+        tiling = {"patch_cells": 16, "vtile": 32} if C * Nv > LARGE_CVU else {}
+        with torch.cuda.stream(stream):
+            g64 = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP64,
+                            stream=stream.cuda_stream, **tiling)
+        ms64, groups64, _ = _time_steps(torch, g64, fp64_steps, 2, dist, local)
+        g64.check()
+        ms64 = _max_over_ranks(torch, dist, ms64) / fp64_steps
+        v64 = ws * C * Nv / (ms64 * 1e-3)
+        g64.close()
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": fp64_steps,
+                "speedup_of_fp32_form": value / v64}
 
     serving_res = None
     if not args.no_serving:
@@ -460,21 +469,21 @@ def main():
         "config": {"workload": args.workload, "cells": C, "nv": Nv, "faces": info["n_faces"],
                    "form": "fp32 storage, fp64 moments", "patch_cells": info["patch_cells"],
                    "vtile": info["vtile"], "gather_threads": info["gather_threads"],
+                   "gather_tile_group": info["gather_tile_group"],
                    "l2": f"inputs larger than L2 (f {info['f_bytes'] / 1e9:.2f} GB per copy)",
                    "w0": "analytic half-range moments" if args.w0_analytic else "discrete half-range sums",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "kernel": "k_gather", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": _gather_traffic(args.workload, info["patch_cells"], info["vtile"],
-                                                info["gather_threads"]),
+                                                info["gather_threads"], info["gather_tile_group"]),
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": g_ms, "group_share": share},
         "alu_roofline": {"bound": "alu", "kernel": "k_gather", "achieved": alu_achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": (alu_achieved / FP32_PEAK_TFLOPS) if alu_achieved else None,
                          "flops_per_cvu": round(flops_cvu, 1), "faces_per_cell": round(nf, 3),
                          "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
-        "fp64_plain": {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": fp64_steps,
-                       "speedup_of_fp32_form": value / v64},
+        "fp64_plain": fp64,
         "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
         "step_hbm_frac_1R1W": value / ws * 4 * nc * 2 / (peak * 1e9),
     }

@@ -103,6 +103,10 @@ typedef struct {
     int32_t vtile;          /* gather tiling: velocities per tile, 32, 64 or 128 (0: automatic) */
     int32_t gather_threads; /* gather tiling: threads per CTA, 256 or 512 (512 only for UGKS_FP32 with
                                vtile <= 64; 0: automatic, 256 unless the autotuner picks 512) */
+    int32_t gather_tile_group; /* gather grid order: the grid sweeps the patches once per group of this
+                               many velocity tiles, the tiles of a patch adjacent, so that a patch's
+                               face data are read once per group (1 .. 1024, larger values are
+                               clamped to the number of tiles; 0: automatic) */
     int32_t w0_analytic;    /* interface equilibrium W0 (Sec. 2.4) from: 0 the discrete half-range
                                sums over the velocity set (default), 1 the analytic half-range
                                moments of the face-state Maxwellians over the continuous velocity
@@ -130,6 +134,7 @@ typedef struct {
     int64_t kernel_launches_per_step;
     int64_t n_wall_faces;               /* faces of type UGKS_FACE_WALL */
     int32_t gather_threads;             /* threads per CTA of the gather pass in use */
+    int32_t gather_tile_group;          /* velocity tiles per group of the gather grid in use */
 } ugks_info_t;
 
 /* Create a case: validates and copies the inputs, orders cells for locality,

@@ -51,7 +51,7 @@ class Params(ct.Structure):
                 ("wall_T", D_P), ("wall_U", D_P), ("inf_rho", ct.c_double),
                 ("inf_U", ct.c_double * 3), ("inf_T", ct.c_double), ("precision", ct.c_int32),
                 ("prim_init", D_P), ("patch_cells", ct.c_int32), ("vtile", ct.c_int32),
-                ("gather_threads", ct.c_int32), ("w0_analytic", ct.c_int32)]
+                ("gather_threads", ct.c_int32), ("gather_tile_group", ct.c_int32), ("w0_analytic", ct.c_int32)]
 
 
 ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_void_p, ct.c_size_t, ct.c_void_p)
@@ -69,7 +69,7 @@ class Info(ct.Structure):
                 ("device_bytes", ct.c_size_t), ("f_bytes", ct.c_size_t), ("n_patches", ct.c_int32),
                 ("patch_cells", ct.c_int32), ("vtile", ct.c_int32),
                 ("kernel_launches_per_step", ct.c_int64), ("n_wall_faces", ct.c_int64),
-                ("gather_threads", ct.c_int32)]
+                ("gather_threads", ct.c_int32), ("gather_tile_group", ct.c_int32)]
 
 
 class Result(ct.Structure):
@@ -150,7 +150,7 @@ def _p(a, typ=D_P):
     return a.ctypes.data_as(typ) if a is not None else None
 
 
-def make_structs(mesh, vgrid, params, init=None, precision=FP64, patch_cells=0, vtile=0, threads=0):
+def make_structs(mesh, vgrid, params, init=None, precision=FP64, patch_cells=0, vtile=0, threads=0, tile_group=0):
     """Marshal the dicts of ``cases`` into ABI structs; returns (structs, keepalive)."""
     keep = []
     D = int(mesh["dim"])
@@ -177,7 +177,7 @@ def make_structs(mesh, vgrid, params, init=None, precision=FP64, patch_cells=0, 
     p = Params(params["Kn"], params.get("L_ref", 1.0), params["Pr"], params["omega"], params["cfl"],
                params.get("dt", 0.0), params.get("limiter", 1), params.get("venkat_K", 1.0), len(walls),
                _p(wT), _p(wU), inf["rho"], (ct.c_double * 3)(*iU), inf["T"], int(precision), _p(ini),
-               int(patch_cells), int(vtile), int(threads), int(params.get("w0_analytic", 0)))
+               int(patch_cells), int(vtile), int(threads), int(tile_group), int(params.get("w0_analytic", 0)))
     return (m, v, p), keep
 
 
@@ -209,13 +209,14 @@ class Case:
     """A UGKS case resident on the GPU (one time step = ``ugks_step``)."""
 
     def __init__(self, mesh, vgrid, params, init=None, precision=FP64, stream=None, torch_alloc=True,
-                 patch_cells=0, vtile=0, threads=0):
+                 patch_cells=0, vtile=0, threads=0, tile_group=0):
         L = load()
         self.D = int(mesh["dim"])
         self.C = len(mesh["cell_vol"])
         self.Nv = len(vgrid["w"])
         self.nc = 2 if self.D == 2 else 1
-        (m, v, p), keep = make_structs(mesh, vgrid, params, init, precision, patch_cells, vtile, threads)
+        (m, v, p), keep = make_structs(mesh, vgrid, params, init, precision, patch_cells, vtile, threads,
+                                       tile_group)
         self._keep = keep
         self._alloc = None
         if torch_alloc:

@@ -119,7 +119,7 @@ struct DevCase {
     double *fsum1, *fsum2;        // [F][S1], [F][S2]
     double *fprim0;               // [F][D+2] rho0, U0, lam0
     double *fqs;                  // [F][5] time integrals q1..q5 of the interface
-    double *dW_part;              // [C][n_vt][D+2]
+    T *dW_part;                   // [C][n_vt][D+2] moments of one velocity tile (sums in T, so exact in T)
     double *res_part;             // [n_res_blocks][2(D+2)]
     int *flags;                   // [1] numeric failure flag
     // tensor-product velocity grid (sep = 1): axes and 1-D weights per dimension
@@ -130,6 +130,7 @@ struct DevCase {
     // gather tiling
     int P, n_patches, n_vt, vtile;
     int nth;                      // threads per gather CTA (256, or 512 for FP32 at TV <= 2)
+    int vt_group;                 // gather grid order: groups of vt_group velocity tiles (see k_gather)
     const int *ring_ptr, *ring_cells;
 };
 

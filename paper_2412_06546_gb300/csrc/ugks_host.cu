@@ -59,7 +59,7 @@ struct ugks_case {
     ugks::DevCase<double> d64{};
     ugks::DevCase<float> d32{};
     ugks::StepConfig cfg{};
-    int P = 0, vtile = 0, nth = 256, n_patches = 0, n_vt = 0;
+    int P = 0, vtile = 0, nth = 256, n_patches = 0, n_vt = 0, vt_group = 1;
     long long *perm_d = nullptr;   // caller cell i -> internal cell
     std::vector<long long> perm_h; // the same on the host
     std::vector<long long> wall_face_h;   // face id of every wall slot
@@ -94,6 +94,20 @@ struct ugks_case {
         blocks.push_back({p, bytes});
         device_bytes += bytes;
         return p;
+    }
+
+    // frees one block of dalloc (the patch arrays of a tiling that is replaced)
+    void dfree(const void *p)
+    {
+        if (!p) return;
+        for (size_t i = 0; i < blocks.size(); ++i)
+            if (blocks[i].first == p) {
+                if (user_alloc) alloc.free(alloc.ctx, blocks[i].first, blocks[i].second, (void *)stream);
+                else cudaFree(blocks[i].first);
+                device_bytes -= blocks[i].second;
+                blocks.erase(blocks.begin() + (long)i);
+                return;
+            }
     }
 
     template <typename V>
@@ -229,6 +243,8 @@ void validate(const ugks_mesh *m, const ugks_vgrid *v, const ugks_params *p)
         fail(UGKS_EINVAL, "gather_threads must be 0, 256 or 512");
     if (p->gather_threads == 512 && (p->precision != UGKS_FP32 || p->vtile > 64))
         fail(UGKS_EINVAL, "gather_threads = 512 needs UGKS_FP32 and vtile <= 64");
+    if (p->gather_tile_group < 0 || p->gather_tile_group > 1024)
+        fail(UGKS_EINVAL, "gather_tile_group must be in [0, 1024]");
 }
 
 // invert the DxD normal matrix by its adjugate
@@ -693,11 +709,12 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     dc.fprim0 = (double *)c->dalloc(Fm * M * sizeof(double));
     dc.fqs = (double *)c->dalloc(Fm * 5 * sizeof(double));
     // sized for the smallest velocity tile, so that the autotuner may retile
-    dc.dW_part = (double *)c->dalloc((size_t)c->C * (c->nvp / 32) * M * sizeof(double));
+    dc.dW_part = (T *)c->dalloc((size_t)c->C * (c->nvp / 32) * M * sizeof(T));
     dc.res_part = (double *)c->dalloc((size_t)c->n_res_blocks * 2 * M * sizeof(double));
     dc.flags = c->flags_d;
     dc.P = c->P;
     dc.nth = c->nth;
+    dc.vt_group = c->vt_group;
     dc.n_patches = c->n_patches;
     dc.n_vt = c->n_vt;
     dc.vtile = c->vtile;
@@ -715,7 +732,7 @@ namespace {
 // (dimension, precision, velocity count, mesh-size bucket) for later cases of
 // the same shape.
 struct Tiling {
-    int P = 0, vtile = 0, nth = 256;
+    int P = 0, vtile = 0, nth = 256, G = 1;
 };
 std::mutex g_tune_mutex;
 std::map<std::string, Tiling> g_tune_cache;
@@ -724,31 +741,38 @@ std::map<std::string, Tiling> g_tune_cache;
 int kDefaultVtile(int prec) { return prec == UGKS_FP64 ? 32 : 64; }
 
 template <typename T>
-void set_tiling(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, int vtile, int nth, size_t smem)
+void set_tiling(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, int vtile, int nth, int G, size_t smem)
 {
     c->P = P;
     c->n_patches = (int)((c->C + P - 1) / P);
     c->vtile = vtile;
     c->nth = nth;
     c->n_vt = (int)(c->nvp / vtile);
+    c->vt_group = std::max(1, std::min(G, c->n_vt));
     c->cfg.smem = smem;
     dc.P = P;
     dc.n_patches = c->n_patches;
     dc.vtile = vtile;
     dc.nth = nth;
     dc.n_vt = c->n_vt;
+    dc.vt_group = c->vt_group;
+    c->dfree(dc.ring_ptr);
+    c->dfree(dc.ring_cells);
+    c->dfree(dc.gi);
     dc.ring_ptr = c->upload(h.ring_ptr);
     dc.ring_cells = c->upload(h.ring_cells);
     dc.gi = reinterpret_cast<const int4 *>(c->upload(h.gi));
 }
 
 template <typename T>
-void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tune_vtile, bool tune_threads)
+void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tune_vtile, bool tune_threads,
+              bool tune_group)
 {
     const size_t esz = sizeof(T);
     char key[160];
-    snprintf(key, sizeof(key), "D%d_nc%d_p%d_vt%d_t%d_nv%lld_c%d", c->D, c->NC, c->prec, tune_vtile ? 0 : c->vtile,
-             tune_threads ? 0 : c->nth, (long long)c->Nv, (int)std::lround(std::log2((double)c->C)));
+    snprintf(key, sizeof(key), "D%d_nc%d_p%d_vt%d_t%d_g%d_nv%lld_c%d", c->D, c->NC, c->prec,
+             tune_vtile ? 0 : c->vtile, tune_threads ? 0 : c->nth, tune_group ? 0 : c->vt_group, (long long)c->Nv,
+             (int)std::lround(std::log2((double)c->C)));
     Tiling best;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -772,6 +796,17 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
         cudaEvent_t e0, e1;
         cuda_ok(cudaEventCreate(&e0), "event");
         cuda_ok(cudaEventCreate(&e1), "event");
+        auto time_gather = [&](size_t smem) {
+            cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
+            cuda_ok(cudaEventRecord(e0, c->stream), "event");
+            for (int r = 0; r < 2; ++r) cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
+            cuda_ok(cudaEventRecord(e1, c->stream), "event");
+            cuda_ok(cudaEventSynchronize(e1), "event");
+            float ms = 0.f;
+            cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "event");
+            return ms;
+        };
+        const int G0 = c->vt_group;
         float best_ms = 0.f;
         for (int nth : tc)
             for (int vt : vc) {
@@ -782,20 +817,30 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
                     build_patches(h, C, P);
                     const size_t smem = smem_of(h, vt);
                     if (smem > (size_t)smem_max) continue;
-                    set_tiling(c, dc, h, P, vt, nth, smem);
-                    cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
-                    cuda_ok(cudaEventRecord(e0, c->stream), "event");
-                    for (int r = 0; r < 2; ++r) cuda_ok(ugks::launch_gather(dc, smem, c->stream), "autotune gather");
-                    cuda_ok(cudaEventRecord(e1, c->stream), "event");
-                    cuda_ok(cudaEventSynchronize(e1), "event");
-                    float ms = 0.f;
-                    cuda_ok(cudaEventElapsedTime(&ms, e0, e1), "event");
+                    set_tiling(c, dc, h, P, vt, nth, G0, smem);
+                    const float ms = time_gather(smem);
                     if (best.P == 0 || ms < best_ms) {
-                        best = {P, vt, nth};
+                        best = {P, vt, nth, G0};
                         best_ms = ms;
                     }
                 }
             }
+        // then the grid order at the chosen tiling: groups of G velocity tiles
+        if (best.P != 0 && tune_group) {
+            build_patches(h, C, best.P);
+            const size_t smem = smem_of(h, best.vtile);
+            set_tiling(c, dc, h, best.P, best.vtile, best.nth, G0, smem);
+            for (int G : {1, 2, 4, 8, 16, 32}) {
+                if (G == G0 || G > c->n_vt) continue;
+                dc.vt_group = G;
+                const float ms = time_gather(smem);
+                if (ms < best_ms) {
+                    best.G = G;
+                    best_ms = ms;
+                }
+            }
+            dc.vt_group = c->vt_group;
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (best.P == 0) return;                 // keep the default tiling
@@ -805,7 +850,9 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
     if (best.P != c->P || best.vtile != c->vtile || best.nth != c->nth) {
         build_patches(h, C, best.P);
         const size_t smem = smem_of(h, best.vtile);
-        if (smem <= (size_t)smem_max) set_tiling(c, dc, h, best.P, best.vtile, best.nth, smem);
+        if (smem <= (size_t)smem_max) set_tiling(c, dc, h, best.P, best.vtile, best.nth, best.G, smem);
+    } else if (best.G != c->vt_group) {
+        c->vt_group = dc.vt_group = best.G;
     }
 }
 
@@ -999,6 +1046,7 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         c->n_patches = (int)((c->C + P - 1) / P);
         c->nvp = (c->Nv + vpad - 1) / vpad * vpad;
         c->n_vt = (int)(c->nvp / c->vtile);
+        c->vt_group = std::max(1, std::min(params->gather_tile_group > 0 ? params->gather_tile_group : 1, c->n_vt));
         c->G = (int)h.gface.size();
         c->NW = (int)h.wface.size();
         c->dt = params->dt > 0.0 ? params->dt : [&] {
@@ -1022,12 +1070,14 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
             fill_case<double>(c.get(), c->d64, mesh, vgrid, params, h);
             cuda_ok(ugks::launch_init(c->d64, c->stream), "init");
             if (params->patch_cells == 0)
-                autotune<double>(c.get(), c->d64, h, smem_max, params->vtile == 0, params->gather_threads == 0);
+                autotune<double>(c.get(), c->d64, h, smem_max, params->vtile == 0, params->gather_threads == 0,
+                                 params->gather_tile_group == 0);
         } else {
             fill_case<float>(c.get(), c->d32, mesh, vgrid, params, h);
             cuda_ok(ugks::launch_init(c->d32, c->stream), "init");
             if (params->patch_cells == 0)
-                autotune<float>(c.get(), c->d32, h, smem_max, params->vtile == 0, params->gather_threads == 0);
+                autotune<float>(c.get(), c->d32, h, smem_max, params->vtile == 0, params->gather_threads == 0,
+                                params->gather_tile_group == 0);
         }
         cuda_ok(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "create sync");
     });
@@ -1245,6 +1295,7 @@ ugks_status ugks_info(const ugks_case *c, ugks_info_t *info)
         info->patch_cells = c->P;
         info->vtile = c->vtile;
         info->gather_threads = c->nth;
+        info->gather_tile_group = c->vt_group;
         info->kernel_launches_per_step = 5 + (c->F > 0 ? 5 : 0) + (c->NW > 0 ? 1 : 0);
         info->n_wall_faces = c->NW;
     });

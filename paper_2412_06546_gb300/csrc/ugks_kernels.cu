@@ -1496,7 +1496,7 @@ __device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, c
         const T sm = warp_transpose_sum<T, NR>(red);
         const int vi = lane >> (NR == 4 ? 3 : 2);
         if ((lane & (NR == 4 ? 7 : 3)) == 0 && vi < M)
-            dc.dW_part[((size_t)c * dc.n_vt + vt) * M + vi] = (double)sm;
+            dc.dW_part[((size_t)c * dc.n_vt + vt) * M + vi] = sm;
     }
 }
 
@@ -1509,7 +1509,16 @@ template <typename T, int D, int NC, int TV, int NTH>
 __global__ void __launch_bounds__(NTH, NTH >= 512 ? 2 : 0) k_gather(DevCase<T> dc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    gather_item<T, D, NC, TV>(dc, blockIdx.x, blockIdx.y, reinterpret_cast<T *>(smem_raw));
+    // One-dimensional grid of n_patches x n_vt blocks in groups of G = vt_group
+    // consecutive velocity tiles: within a group the patches follow each other
+    // and the G tiles of a patch are adjacent, so a patch's face entries and
+    // records are fetched from DRAM once per group, not once per tile, when a
+    // sweep over all patches does not fit L2 (large 3D meshes).  G = 1 is the
+    // plain patch-major sweep of one tile after another.
+    const int G = dc.vt_group, per = dc.n_patches * G;
+    const int grp = blockIdx.x / per, base = grp * G, gsz = min(G, dc.n_vt - base);
+    const int r = blockIdx.x - grp * per;
+    gather_item<T, D, NC, TV>(dc, r / gsz, base + r % gsz, reinterpret_cast<T *>(smem_raw));
 }
 
 // Persistent gather over many cases: a fixed grid of CTAs walks a work list of
@@ -1540,7 +1549,7 @@ __device__ __forceinline__ void update_W_body(const DevCase<T> &dc, const int bx
         double *Wc = dc.W + (size_t)c * M;
         for (int m = 0; m < M; ++m) {
             double s = 0.0;
-            for (int t = 0; t < dc.n_vt; ++t) s += dc.dW_part[((size_t)c * dc.n_vt + t) * M + m];
+            for (int t = 0; t < dc.n_vt; ++t) s += (double)dc.dW_part[((size_t)c * dc.n_vt + t) * M + m];
             wsq[m] = Wc[m] * Wc[m];
             dsq[m] = s * s;
             Wc[m] += s;
@@ -1772,7 +1781,7 @@ static cudaError_t gather_launch(const DevCase<T> &dc, size_t smem, cudaStream_t
     auto kern = k_gather<T, D, NC, TV, NTH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(dc.n_patches, dc.n_vt);
+    const int grid = dc.n_patches * dc.n_vt;
     kern<<<grid, NTH, smem, st>>>(dc);
     return cudaGetLastError();
 }

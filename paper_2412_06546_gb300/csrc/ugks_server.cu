@@ -67,7 +67,7 @@ size_t footprint_estimate(const Request &r)
     const size_t C = (size_t)r.C, F = (size_t)std::max<int64_t>(r.F, 1);
     size_t b = 2 * C * NC * nvp * s;                                   // f_cur, f_nxt
     b += C * (size_t)(M * 2 + D + D * M * 2 + 8) * 8;                  // W, q, prim, gradients, vol
-    b += C * 2 * 12 * s + C * (nvp / 32 + 1) * M * 8;                  // records, residual partials
+    b += C * 2 * 12 * s + C * (nvp / 32 + 1) * M * s;                  // records, residual partials
     b += F * (size_t)(40 * s + 24 * s + 16 * s + (D * M + D + D + M + M + 5) * 8 + 60 * 8 + 64);
     b += 2 * F * (size_t)(8 * D + 24) + C * 64 + nvp * 64;             // geometry, LSQ, patches
     b += 2 * F * (size_t)(16 + 16 * s);                                // gather entries

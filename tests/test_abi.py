@@ -145,3 +145,14 @@ def test_gather_block_size_is_validated(lib, precision, threads, vtile, msg):
     h = ct.c_void_p()
     assert lib.ugks_create(ct.byref(m), ct.byref(v), ct.byref(p), None, None, ct.byref(h)) == 1
     assert msg in lib.ugks_last_error() and not h.value
+
+
+@pytest.mark.parametrize("group", [-1, 1025])
+def test_gather_tile_group_is_validated(lib, group):
+    from paper_2412_06546_gb300 import cases
+    case = cases.cavity_case(n=3, nv=4)
+    (m, v, p), keep = _lib.make_structs(case["mesh"], case["vgrid"], case["params"], case["init"],
+                                        _lib.FP32, 0, 0, 0, group)
+    h = ct.c_void_p()
+    assert lib.ugks_create(ct.byref(m), ct.byref(v), ct.byref(p), None, None, ct.byref(h)) == 1
+    assert b"gather_tile_group must be in [0, 1024]" in lib.ugks_last_error() and not h.value

@@ -314,12 +314,16 @@ def test_limits_and_options(variant):
     _compare(o, g, what=variant)
 
 
-@pytest.mark.parametrize("patch,vtile", [(4, 32), (17, 64), (64, 128), (200, 32)])
-def test_tiling_does_not_change_results(patch, vtile):
+@pytest.mark.parametrize("patch,vtile,group", [(4, 32, 1), (17, 64, 3), (64, 128, 1), (200, 32, 4), (24, 32, 64)])
+def test_tiling_does_not_change_results(patch, vtile, group):
+    """Patch size, velocity tile and the grid's tile groups (5 tiles in groups
+    of 3 and 10 in groups of 4 end with a partial group; 64 is clamped to one
+    group of all tiles) leave the FP64 step at the oracle's values."""
     case = cs.cylinder_case(n_cells=1500, nvx=18, nvy=15, mach=4.0)
-    o, g = _pair(case, perturb=0.05, patch_cells=patch, vtile=vtile)
+    o, g = _pair(case, perturb=0.05, patch_cells=patch, vtile=vtile, tile_group=group)
     info = g.info()
     assert info["patch_cells"] <= patch and info["vtile"] == vtile
+    assert info["gather_tile_group"] == min(group, info["nv_pad"] // vtile)
     o.step(1)
     g.step(1)
     _compare(o, g, what=f"tiling {patch}/{vtile}")
