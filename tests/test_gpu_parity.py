@@ -378,6 +378,28 @@ def test_fp32_storage_form_cavity_100_steps():
     assert eW <= 1e-5 and ef <= 1e-5 and eU <= 1e-4
 
 
+def test_fp32_storage_form_converged_cavity():
+    """The lid-driven cavity (20 x 20 quadrilaterals, 24^2 velocities, Kn 0.075)
+    run to its steady state: 2,400 steps bring the residual below 1e-7 (it
+    falls about 3.3 times per 250 steps).  The converged fields of the
+    FP32-storage form (W, the velocity and the heat flux, each against its
+    own largest magnitude) match the FP64 oracle's to 1e-4."""
+    case = cs.cavity_case()
+    o = oracle.OracleCase(case["mesh"], case["vgrid"], case["params"], case["init"], n_threads=0)
+    g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32)
+    o.step(2400)
+    g.step(2400)
+    ro, rg = np.max(o.residual()), np.max(g.residual())
+    assert ro < 1e-6 and rg < 1e-6, (ro, rg)
+    _, Wo, qo = o.state()
+    _, Wg = g.state(with_f=False)
+    qg = g.heat_flux()
+    Uo, Ug = Wo[:, 1:3] / Wo[:, :1], Wg[:, 1:3] / Wg[:, :1]
+    errs = {"W": _rel_max(Wg, Wo), "U": _rel_max(Ug, Uo), "q": _rel_max(qg, qo)}
+    print(f"fp32 converged cavity: residual {rg:.1e}, " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    assert max(errs.values()) <= 1e-4, errs
+
+
 def test_fp32_storage_form_cylinder_100_steps():
     case = cs.cylinder_case(n_cells=2000, nvx=30, nvy=25, start="impulsive")
     o = oracle.OracleCase(case["mesh"], case["vgrid"], case["params"], case["init"])
