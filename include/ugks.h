@@ -106,7 +106,8 @@ typedef struct {
     int32_t gather_tile_group; /* gather grid order: the grid sweeps the patches once per group of this
                                many velocity tiles, the tiles of a patch adjacent, so that a patch's
                                face data are read once per group (1 .. 1024, larger values are
-                               clamped to the number of tiles; 0: automatic) */
+                               clamped to the number of tiles; 0: chosen by the autotuner when
+                               patch_cells is 0, else 1) */
     int32_t w0_analytic;    /* interface equilibrium W0 (Sec. 2.4) from: 0 the discrete half-range
                                sums over the velocity set (default), 1 the analytic half-range
                                moments of the face-state Maxwellians over the continuous velocity
@@ -114,7 +115,11 @@ typedef struct {
 } ugks_params;
 
 /* Device allocator.  alloc returns a device pointer of at least `bytes`
- * (256-byte aligned) usable on `stream`, or NULL; free releases it. */
+ * (256-byte aligned) usable on `stream`, or NULL; free releases it.  Blocks
+ * are freed by ugks_destroy, and by ugks_create when the autotuner replaces a
+ * tiling's patch arrays; a freed block may still be read by work queued on
+ * `stream` before the free (stream-ordered reuse, as a caching allocator
+ * provides). */
 typedef struct {
     void *ctx;
     void *(*alloc)(void *ctx, size_t bytes, void *stream);
