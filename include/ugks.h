@@ -116,10 +116,9 @@ typedef struct {
 
 /* Device allocator.  alloc returns a device pointer of at least `bytes`
  * (256-byte aligned) usable on `stream`, or NULL; free releases it.  Blocks
- * are freed by ugks_destroy, and by ugks_create when the autotuner replaces a
- * tiling's patch arrays; a freed block may still be read by work queued on
- * `stream` before the free (stream-ordered reuse, as a caching allocator
- * provides). */
+ * are freed by ugks_destroy and by ugks_create when the autotuner replaces a
+ * tiling's patch arrays, in both cases after the case stream has finished the
+ * work that reads them. */
 typedef struct {
     void *ctx;
     void *(*alloc)(void *ctx, size_t bytes, void *stream);

@@ -756,6 +756,10 @@ void set_tiling(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, int vt
     dc.nth = nth;
     dc.n_vt = c->n_vt;
     dc.vt_group = c->vt_group;
+    // the old patch arrays may still be read by queued kernels: drain the
+    // stream first, so that any allocator may reuse them at once
+    if (dc.ring_ptr || dc.ring_cells || dc.gi)
+        cuda_ok(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "retile sync");
     c->dfree(dc.ring_ptr);
     c->dfree(dc.ring_cells);
     c->dfree(dc.gi);
