@@ -56,6 +56,7 @@ struct ugks_case {
     bool user_alloc = false;
     std::vector<std::pair<void *, size_t>> blocks;
     size_t device_bytes = 0, f_bytes = 0;
+    size_t stage_bytes = 0;        // bytes of f_nxt, the staging area of state I/O (>= f_bytes)
     ugks::DevCase<double> d64{};
     ugks::DevCase<float> d32{};
     ugks::StepConfig cfg{};
@@ -612,7 +613,10 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     // state
     const size_t fcount = (size_t)c->C * c->NC * c->nvp;
     dc.f_cur = (T *)c->dalloc(fcount * sizeof(T));
-    dc.f_nxt = (T *)c->dalloc(fcount * sizeof(T));
+    // f_nxt also stages state I/O, in host rows of up to FP64: room for at
+    // least two cells' FP64 rows (one per upload slot), even on tiny meshes
+    c->stage_bytes = std::max(fcount * sizeof(T), (size_t)2 * c->NC * c->nvp * sizeof(double));
+    dc.f_nxt = (T *)c->dalloc(c->stage_bytes);
     c->f_bytes = fcount * sizeof(T);
     std::vector<double> W((size_t)c->C * M);
     for (int64_t i = 0; i < c->C; ++i) {
@@ -894,7 +898,7 @@ template <typename S>
 void export_f(ugks_case *c, S *f)
 {
     const size_t per = (size_t)c->NC * c->Nv;
-    const size_t cap = c->f_bytes / sizeof(S);
+    const size_t cap = c->stage_bytes / sizeof(S);
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>(cap / per, (size_t)c->C));
     for (int c0 = 0; c0 < (int)c->C; c0 += chunk) {
         const int nc = (int)std::min<int64_t>(chunk, c->C - c0);
@@ -919,7 +923,7 @@ template <typename S>
 void import_f(ugks_case *c, const S *f)
 {
     const size_t per = (size_t)c->NC * c->Nv;
-    const size_t slot = c->f_bytes / 2 / sizeof(S);
+    const size_t slot = c->stage_bytes / 2 / sizeof(S);            // >= one cell's row
     int chunk = (int)std::max<size_t>(1, std::min<size_t>(slot / per, (size_t)c->C));
     chunk = std::min(chunk, (int)std::max<int64_t>(1, (c->C + 3) / 4));   // at least four chunks in flight
     if (!c->copy_stream) {
@@ -1226,7 +1230,7 @@ ugks_status ugks_get_cells(ugks_case *c, const int64_t *cells, int64_t n, double
         }
         if (f) {
             const size_t per = (size_t)c->NC * c->Nv;
-            const size_t cap = c->f_bytes / sizeof(double);
+            const size_t cap = c->stage_bytes / sizeof(double);
             const int chunk = (int)std::max<size_t>(1, std::min<size_t>(cap / per, (size_t)n));
             for (int c0 = 0; c0 < (int)n; c0 += chunk) {
                 const int nc = (int)std::min<int64_t>(chunk, n - c0);

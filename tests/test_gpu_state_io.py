@@ -116,3 +116,28 @@ def test_small_case_with_fewer_cells_than_chunks():
     f_back, _ = g.state(f_dtype=np.float32)
     assert np.array_equal(f_back, f2)
     g.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_fp64_state_io_of_tiny_fp32_cases(n):
+    """One to three cells in FP32 storage through the FP64 calls.  A cell's
+    FP64 row (99 velocities: 1,584 B) is larger than its FP32 row (padded
+    to 128: 1,024 B), so it would not fit one FP32 copy of f (n = 1) or one
+    of the two upload slots (n = 2, 3): the staging area is sized for FP64
+    rows.  Round trips through ugks_set_state, ugks_get_state and
+    ugks_get_cells are exact, and the case steps."""
+    mesh = cs.quad_mesh(n, 1, left=("wall", 0), right=("wall", 0), bottom=("wall", 0), top=("wall", 0))
+    case = {"mesh": mesh, "vgrid": cs.cartesian_vgrid((11, 9), (-5, -5), (5, 5)),
+            "params": cs.params(0.5, walls=[{"T": 1.0, "U": [0, 0, 0]}]), "init": cs.uniform_state(n, 2)}
+    g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32)
+    assert g.info()["nv_pad"] == 128
+    f, W = g.state()
+    f2 = (f * cs.perturbation(f.shape, 7, 0.1)).astype(np.float32).astype(np.float64)
+    g.set_state(f2, W)
+    fb, Wb = g.state()
+    assert np.array_equal(fb, f2) and np.array_equal(Wb, W)
+    fc, Wc = g.cells(np.arange(n)[::-1])
+    assert np.array_equal(fc, f2[::-1]) and np.array_equal(Wc, W[::-1])
+    g.step(2)
+    g.check()
+    g.close()
