@@ -78,6 +78,7 @@ def lib():
         L.or_residual.argtypes = [ct.c_void_p, D_P]
         L.or_wall_rho.argtypes = [ct.c_void_p, D_P]
         L.or_face_macro_flux.argtypes = [ct.c_void_p, D_P]
+        L.or_face_states.argtypes = [ct.c_void_p, D_P, D_P]
         L.or_wall_quantities.argtypes = [ct.c_void_p, D_P, D_P, D_P]
         L.or_time_integrals.argtypes = [ct.c_double, ct.c_double, D_P]
         L.or_maxwellian.argtypes = [ct.c_int32, ct.c_double, D_P, ct.c_double, ct.c_int64, D_P, D_P, D_P]
@@ -186,6 +187,14 @@ class OracleCase:
         p, sg, q = np.empty(n), np.empty(n), np.empty(n)
         lib().or_wall_quantities(self._h, _p(p), _p(sg), _p(q))
         return p[:self.n_wall], sg[:self.n_wall], q[:self.n_wall]
+
+    def face_states(self):
+        """W_L, W_R [F][D+2] of the last step (conserved; W_R is the ghost state
+        at far-field faces; zero at walls)."""
+        WL = np.empty((self.F, self.D + 2))
+        WR = np.empty((self.F, self.D + 2))
+        lib().or_face_states(self._h, _p(WL), _p(WR))
+        return WL, WR
 
     def face_macro_flux(self):
         F = np.empty((self.F, self.D + 2))

@@ -57,6 +57,8 @@ struct or_case {
     /* per-step work arrays */
     double *Wold, *q, *rho, *U, *lam, *tau, *gradW, *Wghost, *W0, *fa, *fA, *q0, *qs, *grad_k,
         *Fk, *Fm, *fin, *gfin, *rho_w, *ghost_k, res[MAXM], *P, *Pg, *gradP;
+    /* face states W_L, W_R of the last step (conserved; W_R = ghost state at far field) */
+    double *WLs, *WRs;
 };
 
 /* ------------------------------------------------------------------------ */
@@ -607,6 +609,8 @@ or_case *or_create(const or_mesh *m, const or_vgrid *v, const or_params *p,
     c->fin = (double *)malloc(sizeof(double) * nwk);
     c->gfin = (double *)malloc(sizeof(double) * nwk * D);
     c->rho_w = (double *)calloc((size_t)(c->n_wall ? c->n_wall : 1), sizeof(double));
+    c->WLs = (double *)calloc((size_t)(F ? F : 1) * M, sizeof(double));
+    c->WRs = (double *)calloc((size_t)(F ? F : 1) * M, sizeof(double));
     memset(c->res, 0, sizeof(c->res));
 
     /* initial condition: W^0 from the primitive state, f^0 = Maxwellian(W^0) */
@@ -648,7 +652,7 @@ void or_destroy(or_case *c)
                     c->eps2, c->wall_face, c->wall_slot_of_face, c->f, c->W, c->Wold, c->q,
                     c->rho, c->U, c->lam, c->tau, c->gradW, c->Wghost, c->W0, c->fa, c->fA,
                     c->q0, c->qs, c->grad_k, c->Fk, c->Fm, c->fin, c->gfin, c->rho_w,
-                    c->ghost_k, c->P, c->Pg, c->gradP};
+                    c->ghost_k, c->P, c->Pg, c->gradP, c->WLs, c->WRs};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(c);
 }
@@ -895,6 +899,10 @@ static void one_step(or_case *c)
                         0.5 * (c->gradW[(i * D + d) * M + m] + c->gradW[(j * D + d) * M + m]);
             /* Sec. 3.2: interface heat flux = average of the two cells */
             for (int d = 0; d < D; ++d) c->q0[f * D + d] = 0.5 * (c->q[i * D + d] + c->q[j * D + d]);
+        }
+        for (int m = 0; m < M; ++m) {
+            c->WLs[f * M + m] = WL[m];
+            c->WRs[f * M + m] = WR[m];
         }
         or_face_equilibrium_ex(D, Nv, c->u, c->w, c->face_n + f * D, WL, WR, g0, c->W0 + f * M,
                                c->fa + f * D * M, c->fA + f * M, c->p.w0_analytic);
@@ -1199,6 +1207,16 @@ void or_wall_quantities(const or_case *c, double *p, double *sigma, double *q)
         sigma[s] = sqrt(t2) / c->dt;
         q[s] = Fm[D + 1] / c->dt;
     }
+}
+
+/* face states of the last step: the reconstructed W_L (owner side) and W_R
+ * (neighbour side, or the far-field ghost state) of every non-wall face, as
+ * conserved variables [F][D+2]; zero at wall faces and before the first step */
+void or_face_states(const or_case *c, double *WL, double *WR)
+{
+    const size_t n = (size_t)c->F * (c->D + 2);
+    if (WL) memcpy(WL, c->WLs, sizeof(double) * n);
+    if (WR) memcpy(WR, c->WRs, sizeof(double) * n);
 }
 
 void or_face_macro_flux(const or_case *c, double *F)

@@ -72,6 +72,10 @@ void or_set_state(or_case *c, const double *f, const double *W);
 void or_residual(const or_case *c, double *res);
 /* wall density of each wall face in the last step (face order), may be NULL-safe */
 void or_wall_rho(const or_case *c, double *rho_w);
+/* face states W_L, W_R[F][D+2] (conserved) of the last step: the primitive
+ * reconstruction of each side at the face centre; at far-field faces W_R is the
+ * ghost state (W_inf on inflow faces, the owner's state elsewhere); zero at walls */
+void or_face_states(const or_case *c, double *WL, double *WR);
 /* macroscopic flux of every face in the last step, F[F][D+2] */
 void or_face_macro_flux(const or_case *c, double *F);
 /* p_w, sigma_w, q_w of the last step at every wall face (face order), Sec. 2.5 */
