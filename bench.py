@@ -1,9 +1,12 @@
 """Benchmark of the UGKS hot path on GB300: cell-velocity updates per second.
 
-Default workload: the 2D Mach-5 argon cylinder at Kn 0.1 (seeded Delaunay
-mesh of ~30,000 triangles, 60x50 Cartesian velocity grid), FP32-storage /
-FP64-moment form; the plain FP64 path is timed beside it.  One step = one full
-UGKS time step (all kernels of Algorithm 1) of the whole case.
+Default workload: the 3D Mach-8 X38-like lifting body at Kn 0.005 and 20
+degrees angle of attack (seeded tetrahedral mesh of ~1.05M cells, unstructured
+tetrahedral velocity mesh of ~4,550 cells), the largest configuration that fits
+one GPU, in the FP32-storage / FP64-moment form; the plain FP64 path is timed
+beside it, and the 2D Mach-5 cylinder (~30,000 triangles, 60x50 velocities) is
+reported as a secondary line.  One step = one full UGKS time step (all kernels
+of Algorithm 1) of the whole case.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ugks|reference]
 
@@ -28,9 +31,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-velocity updates/s"
 UNIT = "cvu/s"
-WORKLOAD = "cylinder_Ma5_Kn0.1_tri30k_v60x50"
+WORKLOAD = "x38_Ma8_Kn0.005_tet1.05M_v4548"
+CYLINDER = "cylinder_Ma5_Kn0.1_tri30k_v60x50"
 E2E_MAX_BYTES = 32e9      # largest host copy of f the e2e leg stages in pinned memory
 LARGE_CVU = 2e9           # cases above this many cell-velocities get a fixed FP64 tiling
+X38_SMALL_H0 = 0.2        # first layer of the X38-like mesh for the ~100k-cell profiling instance
 
 
 def _peaks():
@@ -42,9 +47,22 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# FP32 ceiling: 152 SMs x 128 FP32 lanes x 2 flops per FMA at the 2070 MHz
-# maximum SM clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+def _fp32_peak(torch, sm_max_mhz):
+    """FP32 ceiling from the device's unit counts and clock: SMs x 128 FP32
+    lanes x 2 flops per FMA x the maximum SM clock (nvidia-smi's clocks.max.sm,
+    sampled during the run)."""
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = float(sm_max_mhz) if sm_max_mhz else None
+    if not mhz:
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(torch.cuda.current_device()), "--query-gpu=clocks.max.sm",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+            mhz = float(out.stdout.strip().splitlines()[0])
+        except Exception:
+            mhz = None
+    if not mhz:
+        return None, n_sm, None
+    return n_sm * 128 * 2 * mhz * 1e6 / 1e12, n_sm, mhz
 
 
 def _gather_flops_per_cvu(D, NC, nf):
@@ -131,7 +149,7 @@ def _dist(backend="nccl"):
 
 def _workload(name):
     from paper_2412_06546_gb300 import cases
-    if name == WORKLOAD:
+    if name == CYLINDER:
         return cases.cylinder_case(n_cells=30000, nvx=60, nvy=50, mach=5.0, Kn=0.1, seed=2)
     if name == "cylinder_Ma5_Kn0.1_tri8k_v60x50":       # the same flow on 8k cells (profiling captures)
         return cases.cylinder_case(n_cells=8000, nvx=60, nvy=50, mach=5.0, Kn=0.1, seed=2)
@@ -141,8 +159,14 @@ def _workload(name):
         return cases.sphere_case()
     if name == "sphere_Ma4_Kn0.1_tet20k_v28":           # the same flow on 20k cells (profiling captures)
         return cases.sphere_case(n_cells=20000)
-    if name == "x38_Ma8_Kn0.005_tet1.05M_v4548":
+    if name == "cylinder_E1_Ma5_Kn0.1_tri30k_dvs2060":    # the paper's unstructured velocity meshes
+        return cases.cylinder_dvs_case("E1", n_cells=30000)
+    if name == "cylinder_E2_Ma15_Kn0.01_tri30k_dvs3420":
+        return cases.cylinder_dvs_case("E2", n_cells=30000)
+    if name == WORKLOAD:
         return cases.x38_case()
+    if name == "x38_Ma8_Kn0.005_tet100k_v4548":         # the same flow on ~100k cells (profiling captures)
+        return cases.x38_case(h0=X38_SMALL_H0, n_surface=100000)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -190,13 +214,19 @@ def _gather_sources():
         return k[a:b] + fh.read()
 
 
+# committed ncu summaries holding the gather's DRAM traffic per launch, by workload
+TRAFFIC_PROFILES = {CYLINDER: "k_gather_cylinder30k_fp32.md", WORKLOAD: "k_gather_x38_fp32.md"}
+
+
 def _gather_traffic(workload, patch, vtile, threads, group):
-    """DRAM bytes of one gather launch from the committed ncu summary, while
-    the gather's sources and tiling are those the counters were taken on
-    (else None: the kernel changed since)."""
+    """DRAM bytes of one gather launch from the committed ncu summary of the
+    workload, while the gather's sources and tiling are those the counters were
+    taken on (else None: the kernel changed since)."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "k_gather_cylinder30k_fp32.md")
-    if workload != WORKLOAD or not os.path.exists(prof):
+    if workload not in TRAFFIC_PROFILES:
+        return None
+    prof = os.path.join(ROOT, "profiles", TRAFFIC_PROFILES[workload])
+    if not os.path.exists(prof):
         return None
     h = hashlib.sha256()
     h.update(_gather_sources())
@@ -290,7 +320,9 @@ def _serving(args, torch, lib, dist=None, rank=0, ws=1):
     ranks each serves its share of the stream on its own GPU."""
     import numpy as np
     from paper_2412_06546_gb300 import serving
-    reqs = _shard(serving.request_stream(args.serve_n, seed=4), rank, ws)
+    spec = ({"c_lo": 1000, "c_hi": 4000, "n_lo": 16, "n_hi": 32} if args.serve_stream == "small"
+            else {"c_lo": 1000, "c_hi": 40000, "n_lo": 16, "n_hi": 64})
+    reqs = _shard(serving.request_stream(args.serve_n, seed=4, **spec), rank, ws)
     budget = int(args.serve_budget_gb * (1 << 30))
 
     def run(arrivals):
@@ -301,7 +333,10 @@ def _serving(args, torch, lib, dist=None, rank=0, ws=1):
         st = srv.stats()
         res = [srv.poll(t) for t in tickets]
         srv.close()
-        lat = [r["t_done"] - r["t_arrive"] for r in res]
+        # latencies of converged requests first, then of step-limited ones (negated
+        # so that they can be told apart after the ranks are merged)
+        lat = [(r["t_done"] - r["t_arrive"]) * (1 if (r["state"] == lib.REQ_DONE and r["status"] == 0) else -1)
+               for r in res]
         span = max(r["t_done"] for r in res) - t0
         conv = sum(1 for r in res if r["state"] == lib.REQ_DONE and r["status"] == 0)
         return ok, lat, span, st["total_cvu"], conv
@@ -312,27 +347,52 @@ def _serving(args, torch, lib, dist=None, rank=0, ws=1):
     ok1, lat1, span1, cvu1, conv1 = run(arr)
     lat0, span0, cvu0, conv0 = _combine_serving(dist, lat0, span0, cvu0, conv0)
     lat1, span1, cvu1, conv1 = _combine_serving(dist, lat1, span1, cvu1, conv1)
+
+    def pct(lat):
+        ok = [x for x in lat if x >= 0]
+        lim = [-x for x in lat if x < 0]
+        allv = ok + lim
+        return {"p50_s": float(np.percentile(allv, 50)), "p99_s": float(np.percentile(allv, 99)),
+                "converged_p50_s": float(np.percentile(ok, 50)) if ok else None,
+                "converged_p99_s": float(np.percentile(ok, 99)) if ok else None,
+                "step_limited": len(lim)}
+
+    p1, p0 = pct(lat1), pct(lat0)
     return {"requests": args.serve_n, "tol": args.serve_tol, "max_steps": args.serve_max_steps,
             "steps_per_tick": args.serve_tick, "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
-            "arrival_rate_per_s": rate * ws, "p50_s": float(np.percentile(lat1, 50)),
-            "p99_s": float(np.percentile(lat1, 99)), "aggregate_cvu_per_s": cvu1 / span1, "converged": conv1,
+            "arrival_rate_per_s": rate * ws, **p1, "aggregate_cvu_per_s": cvu1 / span1, "converged": conv1,
             "finished": bool(ok1),
-            "closed_run": {"makespan_s": span0, "aggregate_cvu_per_s": cvu0 / span0,
-                           "p50_s": float(np.percentile(lat0, 50)), "p99_s": float(np.percentile(lat0, 99)),
-                           "converged": conv0},
-            "workload": "seeded cavity/cylinder stream: cells 1k-4k, N^2 velocities N in [16, 32], "
-                        "Kn log-uniform [1e-3, 10], Mach [0.1, 6], FP32 storage"}
+            "closed_run": {"makespan_s": span0, "aggregate_cvu_per_s": cvu0 / span0, **p0, "converged": conv0},
+            "workload": (f"seeded cavity/cylinder stream: cells {spec['c_lo']}-{spec['c_hi']}, N^2 velocities "
+                         f"N in [{spec['n_lo']}, {spec['n_hi']}], Kn log-uniform [1e-3, 10], Mach [0.1, 6], "
+                         "FP32 storage; latency = arrival to completion, quantised to ticks of "
+                         f"{args.serve_tick} steps")}
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: every timed step is one oracle
+    step of the bench workload; cases above 3e8 cell-velocities step the local
+    problem of a seeded sample of cells instead (one step of it gives the
+    full-mesh step at the sample; about 5e7 cell-velocities, a second or two
+    per step).  Rank 0 alone runs it."""
     dist_rank = int(os.environ.get("RANK", "0"))
     if dist_rank != 0:
         return 0
     import oracle
+    from paper_2412_06546_gb300 import cases
     oracle.build()
     case = _workload(args.workload)
     cores = os.cpu_count() or 1
-    o = oracle.OracleCase(case["mesh"], case["vgrid"], case["params"], case["init"], n_threads=cores)
+    mesh, C0, Nv0 = case["mesh"], len(case["mesh"]["cell_vol"]), len(case["vgrid"]["w"])
+    if C0 * Nv0 <= 3e8:
+        o = oracle.OracleCase(mesh, case["vgrid"], case["params"], case["init"], n_threads=cores)
+        what = "full steps of the same case"
+    else:
+        n = max(48, min(C0 // 4, int(5e7 / Nv0 / 12)))
+        sub, s2, _ = cases.local_problem(mesh, cases.pick_sample(mesh, n, 1))
+        o = oracle.OracleCase(sub, case["vgrid"], case["params"], case["init"][s2], n_threads=cores)
+        what = (f"steps of the local problem of {n} seeded cells of the same case "
+                f"({len(s2)} of {C0} cells, all {Nv0} velocities)")
     o.step(args.ref_warmup)
     times = []
     for _ in range(args.ref_steps):
@@ -344,27 +404,108 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.ref_steps, "warmup": args.ref_warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "cells": o.C, "nv": o.Nv, "form": "fp64 CPU oracle"},
+            "config": {"workload": args.workload, "cells": C0, "nv": Nv0, "form": "fp64 CPU oracle"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.ref_steps} full steps of the same case after {args.ref_warmup} warm-up"},
+                             "sample": f"{args.ref_steps} {what} after {args.ref_warmup} warm-up, OpenMP"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+def _measure(torch, lib, name, case, args, dist, ws, local, steps, warmup, stream, e2e=False):
+    """FP32-form steps of one workload: cell-velocity updates per second, the
+    kernel-group times of the timed steps, the gather's HBM roofline and its
+    FP32 ceiling, and (e2e) the same metric through the public API with host
+    buffers."""
+    import numpy as np
+    with torch.cuda.stream(stream):
+        g = lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=lib.FP32,
+                     stream=stream.cuda_stream, patch_cells=args.patch, vtile=args.vtile,
+                     threads=args.threads, tile_group=args.tile_group)
+    info = g.info()
+    C, Nv, nc = info["n_cells"], info["nv"], info["ncomp"]
+    ms, groups, clocks = _time_steps(torch, g, steps, warmup, dist, local)
+    g.check()
+    ms = _max_over_ranks(torch, dist, ms)
+    ms_step = ms / steps
+    value = ws * C * Nv / (ms_step * 1e-3)
+    # roofline of the dominant kernel (gather pass): 1 read + 1 write of f
+    peak, peak_kind = _peaks()
+    g_ms = groups.get("gather", 0.0) / max(steps, 1)
+    alg_bytes = 2 * C * nc * Nv * 4
+    achieved = alg_bytes / (g_ms * 1e-3) / 1e9 if g_ms > 0 else None
+    share = {k: round(v / max(sum(groups.values()), 1e-12), 4) for k, v in groups.items()}
+    # the second ceiling: FP32 arithmetic of the gather against the FP32 peak
+    nf = float((np.asarray(case["mesh"]["face_cells"]) >= 0).sum()) / C
+    flops_cvu = _gather_flops_per_cvu(info["dim"], nc, nf)
+    alu_achieved = flops_cvu * C * Nv / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None
+    fp32_peak, n_sm, mhz = _fp32_peak(torch, clocks.get("sm_max_mhz"))
+    out = {
+        "value": value, "ms_per_step": ms_step, "steps": steps, "warmup": warmup, "clocks": clocks,
+        "gpu_launches": info["kernel_launches_per_step"] * steps,
+        "config": {"workload": name, "cells": C, "nv": Nv, "faces": info["n_faces"],
+                   "form": "fp32 storage, fp64 moments", "patch_cells": info["patch_cells"],
+                   "vtile": info["vtile"], "gather_threads": info["gather_threads"],
+                   "gather_tile_group": info["gather_tile_group"],
+                   "l2": f"inputs larger than L2 (f {info['f_bytes'] / 1e9:.2f} GB per copy)",
+                   "w0": "analytic half-range moments" if args.w0_analytic else "discrete half-range sums",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "kernel": "k_gather", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                     "traffic": _gather_traffic(name, info["patch_cells"], info["vtile"],
+                                                info["gather_threads"], info["gather_tile_group"]),
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
+                     "launch_ms": g_ms, "group_share": share},
+        "alu_roofline": {"bound": "alu", "kernel": "k_gather", "achieved": alu_achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s",
+                         "frac": (alu_achieved / fp32_peak) if (alu_achieved and fp32_peak) else None,
+                         "flops_per_cvu": round(flops_cvu, 1), "faces_per_cell": round(nf, 3),
+                         "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {mhz} MHz"},
+        "step_hbm_frac_1R1W": value / ws * 4 * nc * 2 / (peak * 1e9),
+    }
+    f_host_bytes = C * nc * Nv * 4
+    if e2e:
+        if args.no_e2e or args.e2e_steps < 1:
+            out["e2e"] = {"skipped": "not requested"}
+        elif f_host_bytes > E2E_MAX_BYTES:
+            out["e2e"] = {"skipped": f"the host copy of f ({f_host_bytes / 1e9:.1f} GB) exceeds "
+                                     f"{E2E_MAX_BYTES / 1e9:.0f} GB"}
+        else:
+            out["e2e"] = _e2e(torch, g, args, dist, ws, C, Nv, info)
+    g.close()
+    return out, info
+
+
+def _fp64_plain(torch, lib, case, args, dist, ws, local, stream, steps, C, Nv):
+    """The same step in the plain FP64 path (fixed tiling on large cases, where
+    the autotuner's trial launches would take minutes)."""
+    tiling = {"patch_cells": 16, "vtile": 32} if C * Nv > LARGE_CVU else {}
+    with torch.cuda.stream(stream):
+        g64 = lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=lib.FP64,
+                       stream=stream.cuda_stream, **tiling)
+    ms64, _, _ = _time_steps(torch, g64, steps, 2, dist, local)
+    g64.check()
+    ms64 = _max_over_ranks(torch, dist, ms64) / steps
+    g64.close()
+    return {"value": ws * C * Nv / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "steps": steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ugks", choices=["ugks", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--fp64-steps", type=int, default=0, help="steps of the FP64 plain path (0: steps/10)")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=3, help="steps of the FP64 plain path")
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 leg")
+    ap.add_argument("--secondary", default=CYLINDER,
+                    help="workload reported beside the main one ('' for none)")
+    ap.add_argument("--secondary-steps", type=int, default=100)
     ap.add_argument("--ref-steps", type=int, default=0)
-    ap.add_argument("--ref-warmup", type=int, default=0)
+    ap.add_argument("--ref-warmup", type=int, default=-1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-n", type=int, default=24)
     ap.add_argument("--serve-tol", type=float, default=1e-4)
@@ -373,6 +514,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     ap.add_argument("--serve-timeout", type=float, default=240.0)
+    ap.add_argument("--serve-stream", default="small", choices=["small", "config"],
+                    help="small: the fast default stream; config: cells 1k-40k, N up to 64")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--patch", type=int, default=0)
     ap.add_argument("--vtile", type=int, default=0)
@@ -384,13 +527,9 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         args.ref_steps = args.ref_steps or args.steps
-        args.ref_warmup = args.ref_warmup if args.ref_warmup else args.warmup
-        # each oracle step is a full step of the case; bound the run to a few minutes
-        args.ref_steps = min(args.ref_steps, 5)
-        args.ref_warmup = min(args.ref_warmup, 1)
+        args.ref_warmup = args.ref_warmup if args.ref_warmup >= 0 else args.warmup
         return run_reference(args)
 
-    import numpy as np
     import torch
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a GPU (no CPU fallback)")
@@ -399,94 +538,55 @@ def main():
     torch.cuda.set_device(local)
     from paper_2412_06546_gb300 import build, _lib
     build.build()
-    case = _workload(args.workload)
-    if args.w0_analytic:
-        case = dict(case, params=dict(case["params"], w0_analytic=1))
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32,
-                      stream=stream.cuda_stream, patch_cells=args.patch, vtile=args.vtile,
-                      threads=args.threads, tile_group=args.tile_group)
-    info = g.info()
-    C, Nv, nc = info["n_cells"], info["nv"], info["ncomp"]
-    ms, groups, clocks = _time_steps(torch, g, args.steps, args.warmup, dist, local)
-    g.check()
-    ms = _max_over_ranks(torch, dist, ms)
-    ms_step = ms / args.steps
-    value = ws * C * Nv / (ms_step * 1e-3)
-    launches = info["kernel_launches_per_step"] * args.steps
 
-    # roofline of the dominant kernel (gather pass): 1 read + 1 write of f
-    peak, peak_kind = _peaks()
-    g_ms = groups.get("gather", 0.0) / max(args.steps, 1)
-    alg_bytes = 2 * C * nc * Nv * 4
-    achieved = alg_bytes / (g_ms * 1e-3) / 1e9 if g_ms > 0 else None
-    share = {k: round(v / max(sum(groups.values()), 1e-12), 4) for k, v in groups.items()}
-    # the second ceiling: FP32 arithmetic of the gather against the FP32 peak
-    nf = float((np.asarray(case["mesh"]["face_cells"]) >= 0).sum()) / C
-    flops_cvu = _gather_flops_per_cvu(info["dim"], nc, nf)
-    alu_achieved = flops_cvu * C * Nv / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None
+    def load(name):
+        c = _workload(name)
+        if args.w0_analytic:
+            c = dict(c, params=dict(c["params"], w0_analytic=1))
+        return c
 
-    # e2e: state in pinned host memory -> ugks_set_state_f32 -> ugks_step -> ugks_moments
-    f_host_bytes = C * nc * Nv * 4
-    if args.no_e2e or args.e2e_steps < 1:
-        e2e = {"skipped": "not requested"}
-    elif f_host_bytes > E2E_MAX_BYTES:
-        e2e = {"skipped": f"the host copy of f ({f_host_bytes / 1e9:.1f} GB) exceeds {E2E_MAX_BYTES / 1e9:.0f} GB"}
-    else:
-        e2e = _e2e(torch, g, args, dist, ws, C, Nv, info)
-    g.close()
-
-    # the plain FP64 path on the same case (fixed tiling on large cases, where
-    # the autotuner's trial launches would take minutes)
-    fp64_steps = args.fp64_steps or max(3, args.steps // 10)
+    case = load(args.workload)
+    main_res, info = _measure(torch, _lib, args.workload, case, args, dist, ws, local, args.steps, args.warmup,
+                              stream, e2e=True)
+    C, Nv = info["n_cells"], info["nv"]
     fp64 = {"skipped": "not requested"}
     if not args.no_fp64:
-        tiling = {"patch_cells": 16, "vtile": 32} if C * Nv > LARGE_CVU else {}
-        with torch.cuda.stream(stream):
-            g64 = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP64,
-                            stream=stream.cuda_stream, **tiling)
-        ms64, groups64, _ = _time_steps(torch, g64, fp64_steps, 2, dist, local)
-        g64.check()
-        ms64 = _max_over_ranks(torch, dist, ms64) / fp64_steps
-        v64 = ws * C * Nv / (ms64 * 1e-3)
-        g64.close()
-        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": fp64_steps,
-                "speedup_of_fp32_form": value / v64}
+        fp64 = _fp64_plain(torch, _lib, case, args, dist, ws, local, stream, args.fp64_steps, C, Nv)
+        fp64["speedup_of_fp32_form"] = main_res["value"] / fp64["value"]
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(case)
+    del case
+
+    secondary = None
+    if args.secondary and args.secondary != args.workload:
+        sc = load(args.secondary)
+        sres, sinfo = _measure(torch, _lib, args.secondary, sc, args, dist, ws, local, args.secondary_steps,
+                               args.warmup, stream)
+        secondary = {k: sres[k] for k in ("value", "ms_per_step", "steps", "config", "roofline", "alu_roofline",
+                                          "step_hbm_frac_1R1W")}
+        if not args.no_fp64:
+            s64 = _fp64_plain(torch, _lib, sc, args, dist, ws, local, stream, max(3, args.secondary_steps // 10),
+                              sinfo["n_cells"], sinfo["nv"])
+            s64["speedup_of_fp32_form"] = sres["value"] / s64["value"]
+            secondary["fp64_plain"] = s64
+        main_res["gpu_launches"] += sres["gpu_launches"]
 
     serving_res = None
     if not args.no_serving:
         serving_res = _serving(args, torch, _lib, dist, rank, ws)
 
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(case)
-
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "cells": C, "nv": Nv, "faces": info["n_faces"],
-                   "form": "fp32 storage, fp64 moments", "patch_cells": info["patch_cells"],
-                   "vtile": info["vtile"], "gather_threads": info["gather_threads"],
-                   "gather_tile_group": info["gather_tile_group"],
-                   "l2": f"inputs larger than L2 (f {info['f_bytes'] / 1e9:.2f} GB per copy)",
-                   "w0": "analytic half-range moments" if args.w0_analytic else "discrete half-range sums",
-                   "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "hbm", "kernel": "k_gather", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": _gather_traffic(args.workload, info["patch_cells"], info["vtile"],
-                                                info["gather_threads"], info["gather_tile_group"]),
-                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
-                     "launch_ms": g_ms, "group_share": share},
-        "alu_roofline": {"bound": "alu", "kernel": "k_gather", "achieved": alu_achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": (alu_achieved / FP32_PEAK_TFLOPS) if alu_achieved else None,
-                         "flops_per_cvu": round(flops_cvu, 1), "faces_per_cell": round(nf, 3),
-                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
-        "fp64_plain": fp64,
-        "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-        "step_hbm_frac_1R1W": value / ws * 4 * nc * 2 / (peak * 1e9),
+        "metric": METRIC, "value": main_res["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main_res["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": main_res["config"], "roofline": main_res["roofline"], "alu_roofline": main_res["alu_roofline"],
+        "fp64_plain": fp64, "e2e": main_res["e2e"], "clocks": main_res["clocks"],
+        "gpu_launches": main_res["gpu_launches"], "step_hbm_frac_1R1W": main_res["step_hbm_frac_1R1W"],
     }
+    if secondary:
+        line["secondary"] = secondary
     if serving_res:
         line["serving"] = serving_res
     if cpu:

@@ -52,9 +52,13 @@ enum { UGKS_FACE_INTERIOR = 0, UGKS_FACE_WALL = 1, UGKS_FACE_FARFIELD = 2, UGKS_
 
 /* precision of the stored distribution and the per-velocity arithmetic.
  * UGKS_FP64: everything in FP64 (the plain method).
- * UGKS_FP32: f stored and streamed in FP32, per-velocity arithmetic in FP32,
- * velocity-moment sums promoted to FP64 per tile, and FP64 for W, the
- * equilibrium parameters, the heat flux and the collision coefficients. */
+ * UGKS_FP32: f stored and streamed in FP32, per-velocity products in FP32;
+ * every velocity-moment sum (interface W0 and the moments of g0, the wall
+ * density, the heat flux, the moments of the flux residual that update W) is
+ * accumulated with compensation per GPU lane (Kahan, or double-float) and
+ * combined across lanes and velocity tiles in FP64; W, the equilibrium
+ * parameters (rho, U, lambda), the heat flux and the collision coefficients
+ * dt/(2 tau) and 1/(1 + dt/(2 tau)) are formed in FP64. */
 enum { UGKS_FP64 = 0, UGKS_FP32 = 1 };
 
 /* Unstructured physical mesh (Sec. 2.3): cells Omega_i and faces S_ij. */
@@ -284,6 +288,58 @@ ugks_status ugks_server_moments(ugks_server *s, uint64_t ticket, double *rho, do
 ugks_status ugks_server_stats(ugks_server *s, ugks_server_stats_t *out);
 void ugks_server_destroy(ugks_server *s);
 
+/* ---- Domain decomposition (Sec. 3.3, Algorithm 2) ----
+ * A mesh is split into subdomains, each a case of its own (one per GPU, or
+ * several on one GPU).  A subdomain's mesh lists its own cells first, then a
+ * halo of two face rings around them (the cells one explicit step reads:
+ * slopes of the face neighbours, whose limited gradients read the second
+ * ring), with every face of its own cells and of the first ring.  One step of
+ * the subdomain updates its own cells exactly as a step of the whole mesh
+ * would, given the same time step; the halo's values come out wrong and are
+ * replaced before the next step by the owners' values (f^{n+1}, W^{n+1} and the
+ * heat flux q^{n+1}): pack the cells another subdomain needs into a device
+ * buffer, move the buffer (a device copy on one GPU, NCCL send/receive or a
+ * peer copy into the receiver's own buffer across GPUs), unpack it into the
+ * receiving subdomain's halo cells.  The paper overlaps this exchange with the
+ * interior update by non-blocking MPI (Algorithm 2); here the buffers move
+ * between steps on the case streams. */
+
+/* dt = cfl * min_i 2|Omega_i| / sum_f S_f(i) / max_k |u_k| over the first
+ * n_cells cells of the mesh (the CFL step of Algorithm 1, as ugks_create
+ * computes it over all cells).  A subdomain's own cells hold all their faces,
+ * so the minimum of this value over the subdomains (their own cells first) is
+ * the whole mesh's time step; pass it as ugks_params.dt to every subdomain.
+ * Host computation; *dt receives the step. */
+ugks_status ugks_cfl_dt(const ugks_mesh *mesh, const ugks_vgrid *vgrid, double cfl, int64_t n_cells, double *dt);
+
+/* Mark the first n_owned cells (caller order) as the case's own cells: the
+ * residual sums of later steps count only them.  Default: every cell. */
+ugks_status ugks_set_owned(ugks_case *c, int64_t n_owned);
+
+/* Residual sums of the last step over the own cells: sums[m] =
+ * sum_i (W^{n+1}_im - W^n_im)^2 and sums[D+2+m] = sum_i (W^n_im)^2, m < dim+2
+ * (host buffer of 2(dim+2) doubles; zeros before the first step).  Adding the
+ * sums of all subdomains (an all-reduce) and taking sqrt(sums[m]) /
+ * sqrt(sums[D+2+m]) gives ugks_residual of the whole mesh.  Synchronises. */
+ugks_status ugks_residual_sums(ugks_case *c, double *sums);
+
+/* Bytes of one halo row: f of a cell in the storage precision ([ncomp][nv],
+ * FP32 or FP64, padded to 8 bytes), then W [dim+2] and q [dim] in FP64. */
+ugks_status ugks_halo_row_bytes(const ugks_case *c, size_t *bytes);
+
+/* Register halo list `slot` (0 <= slot < 4096): the caller cells cells[0..n)
+ * whose rows ugks_halo_pack writes to, or ugks_halo_unpack reads from, a
+ * buffer in this order.  The list is copied to the device; setting a slot
+ * again replaces it (after the case stream has finished using the old one).
+ * UGKS_EINVAL for an id outside [0, n_cells). */
+ugks_status ugks_halo_set(ugks_case *c, int32_t slot, const int64_t *cells, int64_t n);
+
+/* Write the rows of slot's cells (the current f, W and q) to device_buf
+ * (n x row bytes, 8-byte aligned, caller-owned device memory), or overwrite
+ * slot's cells from such a buffer.  Asynchronous on the case stream. */
+ugks_status ugks_halo_pack(ugks_case *c, int32_t slot, void *device_buf);
+ugks_status ugks_halo_unpack(ugks_case *c, int32_t slot, const void *device_buf);
+
 /* Sizes and tiling of a case. */
 ugks_status ugks_info(const ugks_case *c, ugks_info_t *info);
 
@@ -305,8 +361,10 @@ void ugks_destroy(ugks_case *c);
  * Limit: n_cells <= 2,097,152 (UGKS_EINVAL above it).  The block partial sums
  * live in a fixed 655 KB file-scope device array that every device which loads
  * the library holds until the process exits.  The first call on a device looks
- * up that array's device address (once, with that device current), so make
- * the first call on each device before any stream capture.  All calls share
+ * up that array's device address (with that device current), and so does the
+ * first call after the device's context changed (cudaDeviceReset, or a primary
+ * context released and created again); make the first call on each device, and
+ * the first after such a change, before any stream capture.  All calls share
  * the array: calls whose kernels overlap on the GPU race and give wrong
  * results.  Each call writes every partial it reads, so nothing carries over
  * from an earlier call.  No cudaMalloc, cudaFree or allocating routine is

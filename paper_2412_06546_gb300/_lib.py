@@ -115,6 +115,13 @@ EXPORTS = {
     "ugks_server_moments": (ct.c_int, [ct.c_void_p, ct.c_uint64, D_P, D_P, D_P, D_P]),
     "ugks_server_stats": (ct.c_int, [ct.c_void_p, ct.POINTER(ServerStats)]),
     "ugks_server_destroy": (None, [ct.c_void_p]),
+    "ugks_cfl_dt": (ct.c_int, [ct.POINTER(Mesh), ct.POINTER(VGrid), ct.c_double, ct.c_int64, D_P]),
+    "ugks_set_owned": (ct.c_int, [ct.c_void_p, ct.c_int64]),
+    "ugks_residual_sums": (ct.c_int, [ct.c_void_p, D_P]),
+    "ugks_halo_row_bytes": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_size_t)]),
+    "ugks_halo_set": (ct.c_int, [ct.c_void_p, ct.c_int32, I64_P, ct.c_int64]),
+    "ugks_halo_pack": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
+    "ugks_halo_unpack": (ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p]),
     "ugks_destroy": (None, [ct.c_void_p]),
     "ugks_last_error": (ct.c_char_p, []),
 }
@@ -179,6 +186,15 @@ def make_structs(mesh, vgrid, params, init=None, precision=FP64, patch_cells=0, 
                _p(wT), _p(wU), inf["rho"], (ct.c_double * 3)(*iU), inf["T"], int(precision), _p(ini),
                int(patch_cells), int(vtile), int(threads), int(tile_group), int(params.get("w0_analytic", 0)))
     return (m, v, p), keep
+
+
+def cfl_dt(mesh, vgrid, cfl, n_cells=None):
+    """ugks_cfl_dt: the CFL step over the first ``n_cells`` cells (all by default)."""
+    (m, v, _), keep = make_structs(mesh, vgrid, {"Kn": 1.0, "Pr": 1.0, "omega": 0.5, "cfl": cfl})
+    dt = ct.c_double()
+    n = len(mesh["cell_vol"]) if n_cells is None else int(n_cells)
+    check(load().ugks_cfl_dt(ct.byref(m), ct.byref(v), float(cfl), n, ct.byref(dt)))
+    return dt.value
 
 
 class _TorchAllocator:
@@ -305,6 +321,30 @@ class Case:
 
     def heat_flux(self):
         return self.moments()[3]
+
+    # ---- domain decomposition (subdomain cases)
+    def set_owned(self, n_owned):
+        check(load().ugks_set_owned(self._h, int(n_owned)))
+
+    def residual_sums(self):
+        out = np.empty(2 * (self.D + 2))
+        check(load().ugks_residual_sums(self._h, _p(out)))
+        return out
+
+    def halo_row_bytes(self):
+        b = ct.c_size_t()
+        check(load().ugks_halo_row_bytes(self._h, ct.byref(b)))
+        return b.value
+
+    def halo_set(self, slot, cells):
+        ids = np.ascontiguousarray(cells, dtype=np.int64)
+        check(load().ugks_halo_set(self._h, int(slot), ids.ctypes.data_as(I64_P), len(ids)))
+
+    def halo_pack(self, slot, device_ptr):
+        check(load().ugks_halo_pack(self._h, int(slot), ct.c_void_p(int(device_ptr))))
+
+    def halo_unpack(self, slot, device_ptr):
+        check(load().ugks_halo_unpack(self._h, int(slot), ct.c_void_p(int(device_ptr))))
 
     GROUPS = ("prep", "face", "wall", "gather", "update_W", "collide")
 

@@ -576,6 +576,105 @@ def tet_ball_vgrid(n_target=4548, R=18.9, centres=((0.0, 0.0, 0.0),), h_min=0.6,
     return {"dim": 3, "u": np.ascontiguousarray(u), "w": np.ascontiguousarray(w), "cart_n": [0, 0, 0]}
 
 
+def tri_disk_vgrid(n_target, R, centre=(0.0, 0.0), refine=(((0.0, 0.0), 3.0),), h_fine=0.5, grad=0.3,
+                   seed=6):
+    """Unstructured 2D velocity grid of exactly ``n_target`` triangles: a seeded
+    Delaunay triangulation of the disk |u - centre| <= R, with spacing h_fine
+    inside each refinement disk ``(point, radius)`` of ``refine`` and growing by
+    ``grad`` per unit distance outside them (capped at R/4), with the centroid
+    rule (u_k = centroid, w_k = area of triangle k).  The spacing scale is
+    bisected to the largest triangulation not above the target, and the
+    remaining count is made up by splitting the largest triangles that have an
+    edge on the disk boundary at that edge's midpoint (each split adds one
+    triangle and leaves every other triangle unchanged)."""
+    from scipy.spatial import Delaunay, cKDTree
+    c0 = np.asarray(centre, float)
+    pts_r = [(np.asarray(p, float), float(r)) for p, r in refine]
+
+    def spacing(X, sc):
+        d = np.full(len(X), np.inf)
+        for p, r in pts_r:
+            d = np.minimum(d, np.maximum(np.linalg.norm(X - p, axis=1) - r, 0.0))
+        return sc * np.minimum(h_fine + grad * d, R / 4.0)
+
+    def build(sc):
+        rng = np.random.default_rng(seed)
+        cand = c0 + rng.uniform(-R, R, size=(40000, 2))
+        cand = cand[np.linalg.norm(cand - c0, axis=1) < R - 1e-9]
+        inner = _thin(cand, spacing(cand, sc), rng)
+        th = np.linspace(0.0, 2 * np.pi, 4000, endpoint=False) + rng.uniform(0, 2 * np.pi / 4000)
+        ring = c0 + R * np.stack([np.cos(th), np.sin(th)], axis=1)
+        ring = _thin(ring, spacing(ring, sc), rng)
+        d, _ = cKDTree(ring).query(inner)
+        inner = inner[d > 0.5 * spacing(inner, sc)]
+        X = np.concatenate([inner, ring])
+        return X, Delaunay(X).simplices
+
+    lo, hi = 0.2, 5.0
+    best = None
+    for _ in range(50):
+        mid = math.sqrt(lo * hi)
+        X, tri = build(mid)
+        if len(tri) <= n_target and (best is None or len(tri) > len(best[1])):
+            best = (X, tri)
+        if len(tri) == n_target:
+            break
+        if len(tri) > n_target:
+            lo = mid
+        else:
+            hi = mid
+    X, tri = best
+    X = [tuple(x) for x in X]
+    tri = [list(t) for t in tri]
+    on_ring = {i for i, x in enumerate(X) if abs(np.hypot(x[0] - c0[0], x[1] - c0[1]) - R) < 1e-9 * R}
+
+    def area(t):
+        a, b, c = (np.asarray(X[i]) for i in t)
+        return 0.5 * abs((b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]))
+
+    while len(tri) < n_target:
+        # edges used by one triangle only lie on the boundary of the triangulation
+        count = {}
+        for t in tri:
+            for e in ((t[0], t[1]), (t[1], t[2]), (t[2], t[0])):
+                k = (min(e), max(e))
+                count[k] = count.get(k, 0) + 1
+        cands = [(area(t), ti, (a, b)) for ti, t in enumerate(tri)
+                 for a, b in ((t[0], t[1]), (t[1], t[2]), (t[2], t[0]))
+                 if count[(min(a, b), max(a, b))] == 1 and a in on_ring and b in on_ring]
+        _, ti, (a, b) = max(cands)
+        m = len(X)
+        X.append(tuple(0.5 * (np.asarray(X[a]) + np.asarray(X[b]))))
+        t = tri[ti]
+        o = [v for v in t if v not in (a, b)][0]
+        tri[ti] = [a, m, o]
+        tri.append([m, b, o])
+    X = np.asarray(X)
+    P = X[np.asarray(tri)]
+    w = 0.5 * np.abs((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1])
+                     - (P[:, 1, 1] - P[:, 0, 1]) * (P[:, 2, 0] - P[:, 0, 0]))
+    return {"dim": 2, "u": np.ascontiguousarray(P.mean(axis=1)), "w": np.ascontiguousarray(w),
+            "cart_n": [0, 0, 0]}
+
+
+def cylinder_dvs_vgrid(mach, which="E1", n_target=None, gamma=5.0 / 3.0, T_inf=1.0, T_w=1.0):
+    """The unstructured velocity meshes of the paper's hypersonic cylinder runs:
+    a disk centred at 0.4 (U_inf, 0), refined around rest and around U_inf.
+    E1 (Ma 5, Kn 0.1): 2,060 triangles, radius 6 sqrt(T_s), refinement radius
+    3 sqrt(T) at both points; E2 (Ma 15, Kn 0.01): 3,420 triangles, radius
+    5 sqrt(T_s), refinement radius 5 sqrt(T).  T_s is the stagnation
+    temperature of the free stream."""
+    U = freestream_speed(mach, gamma, T_inf)
+    Ts = T_inf * (1.0 + 0.5 * (gamma - 1.0) * mach * mach)
+    if which == "E1":
+        n, R, rr = 2060, 6.0 * math.sqrt(Ts), 3.0
+    else:
+        n, R, rr = 3420, 5.0 * math.sqrt(Ts), 5.0
+    return tri_disk_vgrid(n_target or n, R, centre=(0.4 * U, 0.0),
+                          refine=(((0.0, 0.0), rr * math.sqrt(T_w)), ((U, 0.0), rr * math.sqrt(T_inf))),
+                          h_fine=0.35 * math.sqrt(T_inf), grad=0.25, seed=6 if which == "E1" else 7)
+
+
 # ----------------------------------------------------------------------------
 # local problems: sampled checks and timings of cases too large for a whole
 # oracle run.  One explicit step updates a cell from data no further than two
@@ -724,6 +823,25 @@ def cylinder_case(n_cells=30000, nvx=60, nvy=50, mach=5.0, Kn=0.1, seed=2,
             "mesh": mesh, "vgrid": vg, "params": pr, "init": init}
 
 
+def cylinder_dvs_case(which="E1", n_cells=30000, seed=2, start="blended"):
+    """The paper's hypersonic cylinder setups on an unstructured velocity mesh:
+    E1 is Ma 5 at Kn 0.1 with the 2,060-triangle velocity mesh, E2 is Ma 15 at
+    Kn 0.01 with the 3,420-triangle one (Kn on the diameter, isothermal wall at
+    T_inf), on the seeded Delaunay cylinder mesh of ``n_cells`` triangles."""
+    mach, Kn = (5.0, 0.1) if which == "E1" else (15.0, 0.01)
+    mesh = cylinder_mesh(n_cells, seed=seed)
+    vg = cylinder_dvs_vgrid(mach, which)
+    Uinf = freestream_speed(mach)
+    pr = params(Kn, L_ref=2.0, walls=[{"T": 1.0, "U": [0.0, 0.0, 0.0]}],
+                inf={"rho": 1.0, "U": [Uinf, 0.0, 0.0], "T": 1.0})
+    if start == "impulsive":
+        init = uniform_state(len(mesh["cell_vol"]), 2, U=[Uinf, 0.0])
+    else:
+        init = blended_start(mesh, [Uinf, 0.0])
+    return {"name": f"cylinder_{which}_Ma{mach:g}_Kn{Kn:g}_c{len(mesh['cell_vol'])}_dvs{len(vg['w'])}",
+            "mesh": mesh, "vgrid": vg, "params": pr, "init": init}
+
+
 def sphere_case(n_cells=150000, nv=28, vmax=10.0, mach=4.0, Kn=0.1, seed=3, start="blended"):
     """3D Mach-``mach`` argon flow past a radius-1 sphere, far field at radius
     12, Kn on the diameter; nv^3 velocities on [-vmax, vmax]^3."""
@@ -741,13 +859,13 @@ def sphere_case(n_cells=150000, nv=28, vmax=10.0, mach=4.0, Kn=0.1, seed=3, star
 
 
 def x38_case(h0=0.0449, nv=4548, mach=8.0, Kn=0.005, aoa_deg=20.0, T_wall=302.0 / 56.0, seed=5,
-             start="blended"):
+             start="blended", n_surface=400000):
     """3D Mach-8 argon flow past the X38-like body at 20 degrees angle of
     attack (the flow meets the flat bottom), Kn 0.005 on the body length 8,
     isothermal wall at T_w = 302/56 T_inf.  Velocities: ``nv`` tetrahedra in
     the ball of radius 4 sqrt(T_s), T_s = 1 + (gamma - 1)/2 Ma^2 the
     stagnation temperature, refined at rest and at U_inf (centroid rule)."""
-    mesh = x38_mesh(h0, seed=seed)
+    mesh = x38_mesh(h0, seed=seed, n_surface=n_surface)
     Uinf = freestream_speed(mach)
     a = math.radians(aoa_deg)
     Uv = [Uinf * math.cos(a), 0.0, Uinf * math.sin(a)]

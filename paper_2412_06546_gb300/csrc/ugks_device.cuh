@@ -20,7 +20,8 @@ constexpr int MAXD = 3;
 constexpr int MAXM = 5;
 
 // cell record: Maxwellian of the cell state plus Shakhov and collision factors
-enum { CR_U = 0, CR_LAM = 3, CR_PREF = 4, CR_KQ = 5, CR_C = 8, CR_NB = 9, CR_NL2 = 10, CREC = 12 };
+// (CR_C = dt / (2 tau) and CR_INV = 1 / (1 + dt / (2 tau)), both formed in FP64)
+enum { CR_U = 0, CR_LAM = 3, CR_PREF = 4, CR_KQ = 5, CR_C = 8, CR_NB = 9, CR_NL2 = 10, CR_INV = 11, CREC = 12 };
 // ghost / side / wall record: a Maxwellian
 enum { GR_U = 0, GR_LAM = 3, GR_PREF = 4, GR_NB = 5, GR_NL2 = 6, GREC = 8 };
 // face record: g0 of the interface, Shakhov factor, time integrals, slopes in
@@ -119,8 +120,10 @@ struct DevCase {
     double *fsum1, *fsum2;        // [F][S1], [F][S2]
     double *fprim0;               // [F][D+2] rho0, U0, lam0
     double *fqs;                  // [F][5] time integrals q1..q5 of the interface
-    T *dW_part;                   // [C][n_vt][D+2] moments of one velocity tile (sums in T, so exact in T)
+    double *dW_part;              // [C][n_vt][D+2] moments of the flux residual over one velocity tile
     double *res_part;             // [n_res_blocks][2(D+2)]
+    const unsigned char *owned;   // [C] 1 for cells whose residual counts (a subdomain's own cells),
+                                  // nullptr: every cell
     int *flags;                   // [1] numeric failure flag
     // tensor-product velocity grid (sep = 1): axes and 1-D weights per dimension
     int sep, cart_n[3];
@@ -182,6 +185,85 @@ __device__ __forceinline__ T warp_sum(T v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// ------------------------------------------------------------ moment sums
+// Velocity-moment sums of the FP32 form are compensated: a lane accumulates
+// its FP32 terms with Kahan's correction (the running sum s and the rounding
+// error c lost so far; the sum is s - c, returned in FP64), and the lanes'
+// sums are combined in FP64.  The FP64 form sums plainly in FP64.  The
+// corrections rely on IEEE rounding of every addition: nothing here may be
+// reassociated or contracted (no fast-math flags).
+template <typename T> struct CSum;
+template <> struct CSum<double> {
+    double s;
+    __device__ __forceinline__ CSum() : s(0.0) {}
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct CSum<float> {
+    float s, c;
+    __device__ __forceinline__ CSum() : s(0.f), c(0.f) {}
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Error-free sum of two FP32 values (Knuth's TwoSum): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float v = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+}
+
+// Double-float addition (hi, lo) += (bh, bl): about 44 significant bits, with
+// FP32 instructions only (FP64 arithmetic is scarce on this part).
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float bh, float bl)
+{
+    float s, e;
+    two_sum(hi, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, bl));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// warp_transpose_sum on double-float pairs (h, l): the same exchange pattern,
+// with every addition a double-float addition.  Returns the full sum of value
+// index lane >> (5 - log2 N) as hi + lo in FP64.
+template <int N>
+__device__ __forceinline__ double warp_transpose_sum_ff(float (&h)[N], float (&l)[N])
+{
+    const int lane = threadIdx.x & 31;
+    int n = N;
+#pragma unroll
+    for (int bit = 16; n > 1; bit >>= 1) {
+        n >>= 1;
+        const bool upper = (lane & bit) != 0;
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            if (i >= n) break;
+            const float sh = upper ? h[i] : h[i + n], sl = upper ? l[i] : l[i + n];
+            const float kh = upper ? h[i + n] : h[i], kl = upper ? l[i + n] : l[i];
+            const float rh = __shfl_xor_sync(0xffffffffu, sh, bit), rl = __shfl_xor_sync(0xffffffffu, sl, bit);
+            h[i] = kh;
+            l[i] = kl;
+            ff_add(h[i], l[i], rh, rl);
+        }
+    }
+    constexpr int used = (N == 8) ? 3 : (N == 4 ? 2 : (N == 2 ? 1 : 0));
+    float rh = h[0], rl = l[0];
+#pragma unroll
+    for (int bit = 16 >> used; bit > 0; bit >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, rh, bit), ol = __shfl_xor_sync(0xffffffffu, rl, bit);
+        ff_add(rh, rl, oh, ol);
+    }
+    return (double)rh + (double)rl;
 }
 
 // Sum of N (4 or 8) values over the 32 lanes of a warp by recursive halving:

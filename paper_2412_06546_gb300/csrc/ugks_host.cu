@@ -76,6 +76,14 @@ struct ugks_case {
     // stream and its events (ready, copied[2], consumed[2])
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t io_ev[5] = {};
+    // domain decomposition: owned-cell mask (internal order) and the halo
+    // lists registered by ugks_halo_set (internal cell ids on the device)
+    unsigned char *owned_d = nullptr;
+    struct HaloList {
+        int *ids = nullptr;
+        int n = 0;
+    };
+    std::vector<HaloList> halo;
 
     void *dalloc(size_t bytes)
     {
@@ -181,8 +189,32 @@ struct Host {
     std::vector<double> fn, frL, frR;
     std::vector<int> ring_ptr, ring_cells;
     int max_slope = 0;
-    double hmin = INFINITY;
 };
+
+// CFL time step of Algorithm 1 over the first n cells of the mesh:
+// dt = cfl * min_i (2 |Omega_i| / sum_f S_f) / max_k |u_k|.  Each cell's face
+// areas are summed in ascending face order, so a cell gives the same value in
+// any mesh that holds all of its faces in the same relative order (a
+// subdomain's own cells).
+double cfl_dt_of(const ugks_mesh *m, const ugks_vgrid *v, double cfl, int64_t n)
+{
+    const int D = m->dim;
+    std::vector<double> sumS((size_t)m->n_cells, 0.0);
+    for (int64_t f = 0; f < m->n_faces; ++f) {
+        sumS[(size_t)m->face_cells[2 * f]] += m->face_S[f];
+        const int64_t b = m->face_cells[2 * f + 1];
+        if (b >= 0) sumS[(size_t)b] += m->face_S[f];
+    }
+    double hmin = INFINITY;
+    for (int64_t i = 0; i < n; ++i) hmin = std::min(hmin, 2.0 * m->cell_vol[i] / sumS[(size_t)i]);
+    double umax = 0.0;
+    for (int64_t k = 0; k < v->nv; ++k) {
+        double s = 0.0;
+        for (int d = 0; d < D; ++d) s += v->u[k * D + d] * v->u[k * D + d];
+        umax = std::max(umax, std::sqrt(s));
+    }
+    return cfl * hmin / umax;
+}
 
 void validate(const ugks_mesh *m, const ugks_vgrid *v, const ugks_params *p)
 {
@@ -422,10 +454,8 @@ void preprocess(const ugks_mesh *m, const ugks_params *p, int P, Host &h)
                 h.nb_a.push_back(s / dd);
             }
         }
-        // limiter scale h_c = 2 D |Omega_c| / sum S; time-step scale
-        // 2 |Omega_c| / sum S bounds |Omega_c| / sum_f S_f (u.n)^+ for |u| = 1
+        // limiter scale h_c = 2 D |Omega_c| / sum S (the time-step scale is cfl_dt_of's)
         const double hc = 2.0 * D * h.vol[c] / sumS;
-        h.hmin = std::min(h.hmin, 2.0 * h.vol[c] / sumS);
         const double Kh = p->venkat_K * hc;
         h.eps2[c] = Kh * Kh * Kh;
     }
@@ -713,9 +743,10 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     dc.fprim0 = (double *)c->dalloc(Fm * M * sizeof(double));
     dc.fqs = (double *)c->dalloc(Fm * 5 * sizeof(double));
     // sized for the smallest velocity tile, so that the autotuner may retile
-    dc.dW_part = (T *)c->dalloc((size_t)c->C * (c->nvp / 32) * M * sizeof(T));
+    dc.dW_part = (double *)c->dalloc((size_t)c->C * (c->nvp / 32) * M * sizeof(double));
     dc.res_part = (double *)c->dalloc((size_t)c->n_res_blocks * 2 * M * sizeof(double));
     dc.flags = c->flags_d;
+    dc.owned = nullptr;
     dc.P = c->P;
     dc.nth = c->nth;
     dc.vt_group = c->vt_group;
@@ -1057,15 +1088,8 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         c->vt_group = std::max(1, std::min(params->gather_tile_group > 0 ? params->gather_tile_group : 1, c->n_vt));
         c->G = (int)h.gface.size();
         c->NW = (int)h.wface.size();
-        c->dt = params->dt > 0.0 ? params->dt : [&] {
-            double umax = 0.0;
-            for (int64_t k = 0; k < c->Nv; ++k) {
-                double s = 0.0;
-                for (int d = 0; d < c->D; ++d) s += vgrid->u[k * c->D + d] * vgrid->u[k * c->D + d];
-                umax = std::max(umax, std::sqrt(s));
-            }
-            return params->cfl * h.hmin / umax;   // upwind CFL bound (the CFL step of Algorithm 1)
-        }();
+        // upwind CFL bound (the CFL step of Algorithm 1)
+        c->dt = params->dt > 0.0 ? params->dt : cfl_dt_of(mesh, vgrid, params->cfl, mesh->n_cells);
         c->n_res_blocks = (int)((c->C + 255) / 256);
         c->cfg.n_res_blocks = c->n_res_blocks;
         c->flags_d = (int *)c->dalloc(sizeof(int));
@@ -1307,6 +1331,112 @@ ugks_status ugks_info(const ugks_case *c, ugks_info_t *info)
         info->kernel_launches_per_step = 5 + (c->F > 0 ? 5 : 0) + (c->NW > 0 ? 1 : 0);
         info->n_wall_faces = c->NW;
     });
+}
+
+ugks_status ugks_cfl_dt(const ugks_mesh *mesh, const ugks_vgrid *vgrid, double cfl, int64_t n_cells, double *dt)
+{
+    return guard([&] {
+        if (!mesh || !vgrid || !dt) fail(UGKS_EINVAL, "mesh, vgrid and dt must not be NULL");
+        if (!(cfl > 0.0)) fail(UGKS_EINVAL, "cfl must be > 0");
+        if (n_cells < 1 || n_cells > mesh->n_cells) fail(UGKS_EINVAL, "n_cells outside [1, mesh n_cells]");
+        if (!mesh->cell_vol || !mesh->face_cells || !mesh->face_S || !vgrid->u || vgrid->nv < 1 ||
+            vgrid->dim != mesh->dim)
+            fail(UGKS_EINVAL, "incomplete mesh or velocity grid");
+        for (int64_t f = 0; f < mesh->n_faces; ++f) {
+            const int64_t a = mesh->face_cells[2 * f], b = mesh->face_cells[2 * f + 1];
+            if (a < 0 || a >= mesh->n_cells || b >= mesh->n_cells) fail(UGKS_EINVAL, "face %lld: cell out of range",
+                                                                       (long long)f);
+        }
+        *dt = cfl_dt_of(mesh, vgrid, cfl, n_cells);
+    });
+}
+
+ugks_status ugks_set_owned(ugks_case *c, int64_t n_owned)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        if (n_owned < 0 || n_owned > c->C) fail(UGKS_EINVAL, "n_owned outside [0, n_cells]");
+        std::vector<unsigned char> mask((size_t)c->C, 0);
+        for (int64_t i = 0; i < n_owned; ++i) mask[(size_t)c->perm_h[(size_t)i]] = 1;
+        if (!c->owned_d) c->owned_d = (unsigned char *)c->dalloc((size_t)c->C);
+        cuda_ok(cudaMemcpyAsync(c->owned_d, mask.data(), mask.size(), cudaMemcpyHostToDevice, c->stream), "upload");
+        cuda_ok(cudaStreamSynchronize(c->stream), "sync");
+        c->d64.owned = c->owned_d;
+        c->d32.owned = c->owned_d;
+    });
+}
+
+ugks_status ugks_residual_sums(ugks_case *c, double *sums)
+{
+    return guard([&] {
+        if (!c || !sums) fail(UGKS_EINVAL, "case and sums must not be NULL");
+        const int M = c->D + 2;
+        for (int i = 0; i < 2 * M; ++i) sums[i] = 0.0;
+        if (!c->stepped) return;
+        std::vector<double> part((size_t)c->n_res_blocks * 2 * M);
+        const double *rp = c->prec == UGKS_FP64 ? c->d64.res_part : c->d32.res_part;
+        cuda_ok(cudaMemcpyAsync(part.data(), rp, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                "residual copy");
+        cuda_ok(cudaStreamSynchronize(c->stream), "residual sync");
+        for (int b = 0; b < c->n_res_blocks; ++b)
+            for (int i = 0; i < 2 * M; ++i) sums[i] += part[(size_t)b * 2 * M + i];
+    });
+}
+
+ugks_status ugks_halo_row_bytes(const ugks_case *c, size_t *bytes)
+{
+    return guard([&] {
+        if (!c || !bytes) fail(UGKS_EINVAL, "case and bytes must not be NULL");
+        const size_t esz = c->prec == UGKS_FP64 ? 8 : 4;
+        const size_t fbytes = ((size_t)c->NC * c->Nv * esz + 7) / 8 * 8;
+        *bytes = fbytes + (size_t)(2 * c->D + 2) * sizeof(double);
+    });
+}
+
+ugks_status ugks_halo_set(ugks_case *c, int32_t slot, const int64_t *cells, int64_t n)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        if (slot < 0 || slot >= 4096) fail(UGKS_EINVAL, "slot outside [0, 4096)");
+        if (n < 0 || n > c->C || (n > 0 && !cells)) fail(UGKS_EINVAL, "invalid cell list");
+        std::vector<int> ids((size_t)n);
+        for (int64_t i = 0; i < n; ++i) {
+            if (cells[i] < 0 || cells[i] >= c->C) fail(UGKS_EINVAL, "cell id %lld out of range", (long long)cells[i]);
+            ids[(size_t)i] = (int)c->perm_h[(size_t)cells[i]];
+        }
+        if ((size_t)slot >= c->halo.size()) c->halo.resize((size_t)slot + 1);
+        auto &h = c->halo[(size_t)slot];
+        if (h.ids) {
+            cuda_ok(cudaStreamSynchronize(c->stream), "sync");   // queued packs may still read the old list
+            c->dfree(h.ids);
+            h.ids = nullptr;
+        }
+        h.n = (int)n;
+        if (n > 0) h.ids = c->upload(ids);
+        cuda_ok(cudaStreamSynchronize(c->stream), "sync");
+    });
+}
+
+static ugks_status halo_move(ugks_case *c, int32_t slot, void *buf, int unpack)
+{
+    return guard([&] {
+        if (!c) fail(UGKS_EINVAL, "case is NULL");
+        if (slot < 0 || (size_t)slot >= c->halo.size()) fail(UGKS_EINVAL, "halo slot %d is not set", slot);
+        const auto &h = c->halo[(size_t)slot];
+        if (h.n > 0 && !buf) fail(UGKS_EINVAL, "buffer must not be NULL");
+        size_t row = 0;
+        ugks_halo_row_bytes(c, &row);
+        with_dc(c, [&](auto &dc) {
+            cuda_ok(ugks::launch_halo(dc, h.ids, h.n, row, buf, unpack, c->stream), unpack ? "halo unpack" : "halo pack");
+        });
+    });
+}
+
+ugks_status ugks_halo_pack(ugks_case *c, int32_t slot, void *device_buf) { return halo_move(c, slot, device_buf, 0); }
+
+ugks_status ugks_halo_unpack(ugks_case *c, int32_t slot, const void *device_buf)
+{
+    return halo_move(c, slot, const_cast<void *>(device_buf), 1);
 }
 
 }  // extern "C"

@@ -13,12 +13,17 @@
 //                 moments of the flux residual                           (velocity loop, Eq. microS1)
 //   k_update_W    W^{n+1} and stage-2 coefficients                       (Eq. macroscopicUpdata)
 //   k_collide     stage 2 and the heat flux of f^{n+1}                   (Eq. microS2)
-// All per-velocity arithmetic is in T (double or float); moment sums are
-// reduced per warp and promoted to FP64; macroscopic scalars are FP64.
+// All per-velocity arithmetic is in T (double or float).  Velocity-moment sums
+// are FP64 in the FP64 form; in the FP32 form each lane's terms are summed with
+// compensation (Kahan, or double-float in the gather's residual moments and the
+// separable prefix sums) and the lanes are combined in FP64.  Macroscopic
+// scalars (W, the equilibrium parameters, the heat flux, the collision
+// coefficients) are formed in FP64.
 #include "ugks_device.cuh"
 #include "ugks_kernels.h"
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 
 namespace ugks {
@@ -176,8 +181,7 @@ __global__ void k_heatflux(DevCase<T> dc)
     Prim p = prim_of(dc.W + (size_t)c * (D + 2), D);
     T U[3] = {(T)p.U[0], (T)p.U[1], (T)p.U[2]};
     const size_t rs = (size_t)NC * dc.nvp;
-    T acc[D];
-    for (int d = 0; d < D; ++d) acc[d] = 0;
+    CSum<T> acc[D];
     for (int k = lane; k < dc.nvp; k += 32) {
         T cc[D], c2 = 0;
         for (int d = 0; d < D; ++d) {
@@ -187,11 +191,11 @@ __global__ void k_heatflux(DevCase<T> dc)
         T h = dc.f_cur[(size_t)c * rs + k];
         T e = c2 * h + (NC == 2 ? dc.f_cur[(size_t)c * rs + dc.nvp + k] : T(0));
         T we = dc.w[k] * e;
-        for (int d = 0; d < D; ++d) acc[d] += cc[d] * we;
+        for (int d = 0; d < D; ++d) acc[d].add(cc[d] * we);
     }
     for (int d = 0; d < D; ++d) {
-        T s = warp_sum(acc[d]);
-        if (lane == 0) dc.q[(size_t)c * D + d] = 0.5 * (double)s;
+        const double s = warp_sum(acc[d].value());
+        if (lane == 0) dc.q[(size_t)c * D + d] = 0.5 * s;
     }
 }
 
@@ -216,7 +220,9 @@ __device__ __forceinline__ void prep_body(const DevCase<T> &dc, const int bx)
         r[CR_LAM] = (T)p.lam;
         r[CR_PREF] = (T)pref_of(p.rho, p.lam, D);
         for (int d = 0; d < 3; ++d) r[CR_KQ + d] = d < D ? (T)(kappa * dc.q[(size_t)c * D + d]) : T(0);
-        r[CR_C] = (T)(0.5 * dc.dt / tau);
+        const double cc = 0.5 * dc.dt / tau;
+        r[CR_C] = (T)cc;
+        r[CR_INV] = (T)(1.0 / (1.0 + cc));
         r[CR_NB] = (T)(dc.nxi / (2.0 * p.lam));
         r[CR_NL2] = (T)(-p.lam * LOG2E);
         return;
@@ -460,6 +466,9 @@ __global__ void k_face_pre_batch(const DevCase<T> *__restrict__ cases, const int
     face_pre_body<T, D, NC>(dc, bx);
 }
 
+// terms per lane that the FP32 face sums add directly before compensating
+constexpr int SUM_BLOCK = 4;
+
 // half-range moments: sum_k w psi_c [H(u_n) g_L + (1 - H(u_n)) g_R], centred at U_ref
 template <typename T, int D, int NC>
 __device__ __forceinline__ void face_sum1_body(const DevCase<T> &dc, const int bx)
@@ -475,35 +484,48 @@ __device__ __forceinline__ void face_sum1_body(const DevCase<T> &dc, const int b
         n[d] = dc.fn[(size_t)f * D + d];
         Ur[d] = (T)dc.fUref[(size_t)f * D + d];
     }
-    T acc[M];
-    for (int m = 0; m < M; ++m) acc[m] = 0;
-    for (int k = lane; k < dc.nvp; k += 32) {
-        T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
-        T un = normal_velocity<T, D>(u, n);
-        T h, b;
-        if (un != T(0)) {
-            const T *s = un > T(0) ? sL : sR;
-            h = maxwell_h<T, D>(s, u);
-            b = s[GR_NB] * h;
-        } else {
-            T hl = maxwell_h<T, D>(sL, u), hr = maxwell_h<T, D>(sR, u);
-            h = T(0.5) * hl + T(0.5) * hr;
-            b = T(0.5) * sL[GR_NB] * hl + T(0.5) * sR[GR_NB] * hr;
+    // FP32 form: blocks of SUM_BLOCK terms of a lane are summed directly, the
+    // block sums compensated (CSum), the lanes combined in FP64
+    constexpr int B = std::is_same<T, float>::value ? SUM_BLOCK : 1;
+    CSum<T> acc[M];
+    for (int k0 = lane; k0 < dc.nvp; k0 += 32 * B) {
+        T blk[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) blk[m] = 0;
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int k = k0 + 32 * j;
+            if (B > 1 && k >= dc.nvp) break;
+            T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
+            T un = normal_velocity<T, D>(u, n);
+            T h, b;
+            if (un != T(0)) {
+                const T *s = un > T(0) ? sL : sR;
+                h = maxwell_h<T, D>(s, u);
+                b = s[GR_NB] * h;
+            } else {
+                T hl = maxwell_h<T, D>(sL, u), hr = maxwell_h<T, D>(sR, u);
+                h = T(0.5) * hl + T(0.5) * hr;
+                b = T(0.5) * sL[GR_NB] * hl + T(0.5) * sR[GR_NB] * hr;
+            }
+            T wk = dc.w[k];
+            T c2 = 0;
+            T wh = wk * h;
+            blk[0] += wh;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                T c = u[d] - Ur[d];
+                c2 += c * c;
+                blk[1 + d] += c * wh;
+            }
+            blk[D + 1] += T(0.5) * wk * (c2 * h + b);
         }
-        T wk = dc.w[k];
-        T c2 = 0;
-        T wh = wk * h;
-        acc[0] += wh;
-        for (int d = 0; d < D; ++d) {
-            T c = u[d] - Ur[d];
-            c2 += c * c;
-            acc[1 + d] += c * wh;
-        }
-        acc[D + 1] += T(0.5) * wk * (c2 * h + b);
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc[m].add(blk[m]);
     }
     for (int m = 0; m < M; ++m) {
-        T s = warp_sum(acc[m]);
-        if (lane == 0) dc.fsum1[(size_t)f * M + m] = (double)s;
+        const double s = warp_sum(acc[m].value());
+        if (lane == 0) dc.fsum1[(size_t)f * M + m] = s;
     }
 }
 
@@ -532,18 +554,59 @@ __global__ void k_face_sum1_batch(const DevCase<T> *__restrict__ cases, const in
 // (NL + 1) doubles per warp.
 constexpr int SUM1_SEP_WARPS = 4;
 
+// Prefix-sum element of k_face_sum1_sep: FP64 in the FP64 form, a
+// double-float pair (hi, lo) in the FP32 form, so that the range sums, which
+// are differences of prefix sums, keep about 44 significant bits.
+template <typename T> struct PSum;
+template <> struct PSum<double> {
+    using type = double;
+    static __device__ __forceinline__ double make(double x) { return x; }
+    static __device__ __forceinline__ void add(double &a, double b) { a += b; }
+    static __device__ __forceinline__ double shfl_up(double a, int o) { return __shfl_up_sync(0xffffffffu, a, o); }
+    static __device__ __forceinline__ double shfl(double a, int l) { return __shfl_sync(0xffffffffu, a, l); }
+    // (a1 - a0) + (b1 - b0) / 2
+    static __device__ __forceinline__ double range(double a1, double a0, double b1, double b0)
+    {
+        return (a1 - a0) + 0.5 * (b1 - b0);
+    }
+};
+template <> struct PSum<float> {
+    using type = float2;
+    static __device__ __forceinline__ float2 make(float x) { return make_float2(x, 0.f); }
+    static __device__ __forceinline__ void add(float2 &a, float2 b) { ff_add(a.x, a.y, b.x, b.y); }
+    static __device__ __forceinline__ float2 shfl_up(float2 a, int o)
+    {
+        return make_float2(__shfl_up_sync(0xffffffffu, a.x, o), __shfl_up_sync(0xffffffffu, a.y, o));
+    }
+    static __device__ __forceinline__ float2 shfl(float2 a, int l)
+    {
+        return make_float2(__shfl_sync(0xffffffffu, a.x, l), __shfl_sync(0xffffffffu, a.y, l));
+    }
+    static __device__ __forceinline__ float range(float2 a1, float2 a0, float2 b1, float2 b0)
+    {
+        float h = a1.x, l = a1.y;
+        ff_add(h, l, -a0.x, -a0.y);
+        float bh = b1.x, bl = b1.y;
+        ff_add(bh, bl, -b0.x, -b0.y);
+        ff_add(h, l, 0.5f * bh, 0.5f * bl);
+        return __fadd_rn(h, l);
+    }
+};
+
 template <typename T, int D, int NC>
 __device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const int bx)
 {
+    using PS = PSum<T>;
+    using E = typename PS::type;
     extern __shared__ __align__(16) unsigned char psum_raw[];
-    T *psum = reinterpret_cast<T *>(psum_raw);
+    E *psum = reinterpret_cast<E *>(psum_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int f = bx * SUM1_SEP_WARPS + warp;
     constexpr int M = D + 2;
     constexpr int L = D - 1;                 // the prefix-sum axis
     const int NL = dc.cart_n[L];
     if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
-    T *P = psum + (size_t)warp * 6 * (NL + 1);
+    E *P = psum + (size_t)warp * 6 * (NL + 1);
     const T *side[2] = {dc.fside + (size_t)f * 2 * GREC, dc.fside + (size_t)f * 2 * GREC + GREC};
     T n[D], Ur[D];
     for (int d = 0; d < D; ++d) {
@@ -553,30 +616,33 @@ __device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const i
     // prefix sums over the last axis of w g (u - Ur)^p, p = 0, 1, 2, per side
     for (int s = 0; s < 2; ++s) {
         const T *r = side[s];
-        T *Ps = P + s * 3 * (NL + 1);
-        if (lane == 0) Ps[0] = Ps[NL + 1] = Ps[2 * (NL + 1)] = T(0);
-        T carry[3] = {0, 0, 0};
+        E *Ps = P + s * 3 * (NL + 1);
+        if (lane == 0) Ps[0] = Ps[NL + 1] = Ps[2 * (NL + 1)] = PS::make(T(0));
+        E carry[3] = {PS::make(T(0)), PS::make(T(0)), PS::make(T(0))};
         for (int j0 = 0; j0 < NL; j0 += 32) {
             const int j = j0 + lane;
-            T v[3] = {0, 0, 0};
+            T x[3] = {0, 0, 0};
             if (j < NL) {
                 const T a = dc.axis[L][j];
                 const T dv = a - r[GR_U + L];
                 const T g = dc.axw[L][j] * gauss<T>(r[GR_LAM], r[GR_NL2], dv * dv);
                 const T c = a - Ur[L];
-                v[0] = g;
-                v[1] = g * c;
-                v[2] = g * c * c;
+                x[0] = g;
+                x[1] = g * c;
+                x[2] = g * c * c;
             }
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
+                E v = PS::make(x[p]);
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const T t = __shfl_up_sync(0xffffffffu, v[p], o);
-                    if (lane >= o) v[p] += t;
+                    const E t = PS::shfl_up(v, o);
+                    if (lane >= o) PS::add(v, t);
                 }
-                if (j < NL) Ps[p * (NL + 1) + j + 1] = carry[p] + v[p];
-                carry[p] += __shfl_sync(0xffffffffu, v[p], 31);
+                E tot = carry[p];
+                PS::add(tot, v);
+                if (j < NL) Ps[p * (NL + 1) + j + 1] = tot;
+                PS::add(carry[p], PS::shfl(v, 31));
             }
         }
     }
@@ -585,9 +651,7 @@ __device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const i
     const T *aL = dc.axis[L];
     int nouter = dc.cart_n[0];
     if (D == 3) nouter *= dc.cart_n[1];
-    T acc[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) acc[m] = 0;
+    CSum<T> acc[M];
     for (int o = lane; o < nouter; o += 32) {
         int idx[2] = {o % dc.cart_n[0], D == 3 ? o / dc.cart_n[0] : 0};
         T uo[2];
@@ -619,14 +683,14 @@ __device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const i
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const T *r = side[s];
-            const T *Ps = P + s * 3 * (NL + 1);
+            const E *Ps = P + s * 3 * (NL + 1);
             const bool lo_side = (s == 0) != asc;        // the full range starts at 0
             const int f0 = lo_side ? 0 : jb, f1 = lo_side ? ja : NL;
             T Y[3];
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
-                const T *Pp = Ps + p * (NL + 1);
-                Y[p] = (Pp[f1] - Pp[f0]) + T(0.5) * (Pp[jb] - Pp[ja]);
+                const E *Pp = Ps + p * (NL + 1);
+                Y[p] = (T)PS::range(Pp[f1], Pp[f0], Pp[jb], Pp[ja]);
             }
             T go = r[GR_PREF];
 #pragma unroll
@@ -635,17 +699,17 @@ __device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const i
                 go *= dc.axw[e][idx[e]] * gauss<T>(r[GR_LAM], r[GR_NL2], dv * dv);
             }
             const T g = go;
-            acc[0] += g * Y[0];
+            acc[0].add(g * Y[0]);
 #pragma unroll
-            for (int e = 0; e < D - 1; ++e) acc[1 + e] += g * co[e] * Y[0];
-            acc[1 + L] += g * Y[1];
-            acc[D + 1] += T(0.5) * g * (co2 * Y[0] + Y[2] + r[GR_NB] * Y[0]);
+            for (int e = 0; e < D - 1; ++e) acc[1 + e].add(g * co[e] * Y[0]);
+            acc[1 + L].add(g * Y[1]);
+            acc[D + 1].add(T(0.5) * g * (co2 * Y[0] + Y[2] + r[GR_NB] * Y[0]));
         }
     }
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-        const T sm = warp_sum(acc[m]);
-        if (lane == 0) dc.fsum1[(size_t)f * M + m] = (double)sm;
+        const double sm = warp_sum(acc[m].value());
+        if (lane == 0) dc.fsum1[(size_t)f * M + m] = sm;
     }
 }
 
@@ -833,40 +897,51 @@ __device__ __forceinline__ void face_sum2_body(const DevCase<T> &dc, const int b
     for (int d = 0; d < D; ++d) U0[d] = fr[FR_U + d];
     const T lam = fr[FR_LAM], pref = fr[FR_PREF], nl2 = fr[FR_NL2];
     using Mo = Mono<D>;
-    T r[Mo::N];
+    // FP32 form: blocks of SUM_BLOCK terms summed directly, block sums
+    // compensated, lanes combined in FP64 (as in k_face_sum1)
+    constexpr int B = std::is_same<T, float>::value ? SUM_BLOCK : 1;
+    CSum<T> r[Mo::N];
+    for (int k0 = lane; k0 < dc.nvp; k0 += 32 * B) {
+        T blk[Mo::N];
 #pragma unroll
-    for (int i = 0; i < Mo::N; ++i) r[i] = 0;
-    for (int k = lane; k < dc.nvp; k += 32) {
-        T c[D], c2 = 0;
+        for (int i = 0; i < Mo::N; ++i) blk[i] = 0;
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            c[d] = dc.u[d][k] - U0[d];
-            c2 += c[d] * c[d];
-        }
-        const T a = dc.w[k] * pref * gauss<T>(lam, nl2, c2);
-        r[0] += a;
+        for (int j = 0; j < B; ++j) {
+            const int k = k0 + 32 * j;
+            if (B > 1 && k >= dc.nvp) break;
+            T c[D], c2 = 0;
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const T a1 = a * c[d];
-            r[Mo::O1 + d] += a1;
-#pragma unroll
-            for (int e = d; e < D; ++e) {
-                const T a2 = a1 * c[e];
-                r[Mo::O2 + pair_index(D, d, e)] += a2;
-                r[Mo::OQ2 + pair_index(D, d, e)] += a2 * c2;
-#pragma unroll
-                for (int g = e; g < D; ++g) r[Mo::O3 + triple_index(D, d, e, g)] += a2 * c[g];
+            for (int d = 0; d < D; ++d) {
+                c[d] = dc.u[d][k] - U0[d];
+                c2 += c[d] * c[d];
             }
-        }
-        const T a4 = a * c2 * c2;
-        r[Mo::OQ4] += a4;
+            const T a = dc.w[k] * pref * gauss<T>(lam, nl2, c2);
+            blk[0] += a;
 #pragma unroll
-        for (int d = 0; d < D; ++d) r[Mo::OQ4 + 1 + d] += a4 * c[d];
+            for (int d = 0; d < D; ++d) {
+                const T a1 = a * c[d];
+                blk[Mo::O1 + d] += a1;
+#pragma unroll
+                for (int e = d; e < D; ++e) {
+                    const T a2 = a1 * c[e];
+                    blk[Mo::O2 + pair_index(D, d, e)] += a2;
+                    blk[Mo::OQ2 + pair_index(D, d, e)] += a2 * c2;
+#pragma unroll
+                    for (int g = e; g < D; ++g) blk[Mo::O3 + triple_index(D, d, e, g)] += a2 * c[g];
+                }
+            }
+            const T a4 = a * c2 * c2;
+            blk[Mo::OQ4] += a4;
+#pragma unroll
+            for (int d = 0; d < D; ++d) blk[Mo::OQ4 + 1 + d] += a4 * c[d];
+        }
+#pragma unroll
+        for (int i = 0; i < Mo::N; ++i) r[i].add(blk[i]);
     }
 #pragma unroll
     for (int i = 0; i < Mo::N; ++i) {
-        const T sm = warp_sum(r[i]);
-        if (lane == 0) dc.fsum2[(size_t)f * S2 + i] = (double)sm;
+        const double sm = warp_sum(r[i].value());
+        if (lane == 0) dc.fsum2[(size_t)f * S2 + i] = sm;
     }
 }
 
@@ -902,20 +977,20 @@ __device__ __forceinline__ void face_sum2_sep_body(const DevCase<T> &dc, const i
     double *out = dc.fsum2 + (size_t)f * NS * (D + 1);
     for (int d = 0; d < D; ++d) {
         const T U0 = fr[FR_U + d];
-        T acc[6] = {0, 0, 0, 0, 0, 0};
+        CSum<T> acc[6];
         for (int i = lane; i < dc.cart_n[d]; i += 32) {
             const T c = dc.axis[d][i] - U0;
             T v = dc.axw[d][i] * gauss<T>(lam, nl2, c * c);
 #pragma unroll
             for (int pw = 0; pw < 6; ++pw) {
-                acc[pw] += v;
+                acc[pw].add(v);
                 v *= c;
             }
         }
 #pragma unroll
         for (int pw = 0; pw < 6; ++pw) {
-            const T sm = warp_sum(acc[pw]);
-            if (lane == pw) out[d * 6 + pw] = (double)sm;
+            const double sm = warp_sum(acc[pw].value());
+            if (lane == pw) out[d * 6 + pw] = sm;
         }
     }
 }
@@ -1181,7 +1256,7 @@ __device__ __forceinline__ void wall_sum_body(const DevCase<T> &dc, const int bx
 {
     constexpr int M = D + 2;
     constexpr int NR = 2 + 2 * M;               // num, den, outgoing moments A, incoming moments B
-    __shared__ T red[NR][8];
+    __shared__ double red[NR][8];
     const int s = bx;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (s >= dc.NW) return;
@@ -1208,9 +1283,7 @@ __device__ __forceinline__ void wall_sum_body(const DevCase<T> &dc, const int bx
     // num / den: zero net mass flux (Eq. maxWalldes); A / B: moments (Eq.
     // macroscopicFlux) of the outgoing flux and of the incoming flux of the
     // unit-density wall Maxwellian over the step, so that F_w = A + rho_w B
-    T v[NR];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) v[i] = 0;
+    CSum<T> v[NR];
     for (int k = threadIdx.x; k < dc.nvp; k += blockDim.x) {
         T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
         T un = normal_velocity<T, D>(u, n);
@@ -1224,7 +1297,7 @@ __device__ __forceinline__ void wall_sum_body(const DevCase<T> &dc, const int bx
                 hin += g[0][d] * r[d];
                 ug += u[d] * g[0][d];
             }
-            v[0] += dc.w[k] * un * (hin - hdt * ug);
+            v[0].add(dc.w[k] * un * (hin - hdt * ug));
             Fh = dt * un * (hin - hdt * ug);
             if (NC == 2) {
                 T bin = dc.f_cur[(size_t)c * rs + (size_t)(NC - 1) * dc.nvp + k], ugb = 0;
@@ -1237,7 +1310,7 @@ __device__ __forceinline__ void wall_sum_body(const DevCase<T> &dc, const int bx
             off = 2;
         } else if (un < T(0)) {
             const T H = maxwell_h<T, D>(wr, u);
-            v[1] += dc.w[k] * un * H;
+            v[1].add(dc.w[k] * un * H);
             Fh = dt * un * H;
             Fb = wr[GR_NB] * Fh;
             off = 2 + M;
@@ -1252,14 +1325,14 @@ __device__ __forceinline__ void wall_sum_body(const DevCase<T> &dc, const int bx
             mom[D + 1] = T(0.5) * wk * (u2 * Fh + (NC == 2 ? Fb : T(0)));
 #pragma unroll
             for (int i = 0; i < M; ++i) {
-                if (off == 2) v[2 + i] += mom[i];
-                else v[2 + M + i] += mom[i];
+                if (off == 2) v[2 + i].add(mom[i]);
+                else v[2 + M + i].add(mom[i]);
             }
         }
     }
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
-        const T t = warp_sum(v[i]);
+        const double t = warp_sum(v[i].value());
         if (lane == 0) red[i][warp] = t;
     }
     __syncthreads();
@@ -1267,7 +1340,7 @@ __device__ __forceinline__ void wall_sum_body(const DevCase<T> &dc, const int bx
         double a[NR];
         for (int i = 0; i < NR; ++i) {
             a[i] = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a[i] += (double)red[i][w];
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a[i] += red[i][w];
         }
         const double rw = -a[0] / a[1];
         dc.rho_w[s] = rw;
@@ -1467,9 +1540,14 @@ __device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, c
         const T cc = cr[CR_C];
         T wk[TV];
         ldv<T, TV>(dc.w + kl, wk);
-        T mom[M];
+        // moments sum_k w psi_k R_k of this tile: FP64 sums in the FP64 form;
+        // in the FP32 form each term is an FP32 product, and the sums over the
+        // lane's velocities and across the warp are double-float (error-free
+        // additions), widened to FP64 for the W update
+        constexpr int NR = M <= 4 ? 4 : 8;
+        T mh[NR], ml[NR];
 #pragma unroll
-        for (int i = 0; i < M; ++i) mom[i] = 0;
+        for (int i = 0; i < NR; ++i) mh[i] = ml[i] = T(0);
         T out[NC][TV];
 #pragma unroll
         for (int j = 0; j < TV; ++j) {
@@ -1482,18 +1560,26 @@ __device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, c
 #pragma unroll
             for (int d = 0; d < D; ++d) u2 += uj[d] * uj[d];
             const T wr0 = wk[j] * R[0][j];
-            mom[0] += wr0;
+            T x[M];
+            x[0] = wr0;
 #pragma unroll
-            for (int d = 0; d < D; ++d) mom[1 + d] += uj[d] * wr0;
-            mom[D + 1] += T(0.5) * (u2 * wr0 + (NC == 2 ? wk[j] * R[NC - 1][j] : T(0)));
+            for (int d = 0; d < D; ++d) x[1 + d] = uj[d] * wr0;
+            x[D + 1] = T(0.5) * (u2 * wr0 + (NC == 2 ? wk[j] * R[NC - 1][j] : T(0)));
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                if constexpr (std::is_same<T, float>::value) {
+                    if (j == 0) mh[i] = x[i];
+                    else ff_add(mh[i], ml[i], x[i], 0.f);
+                } else {
+                    mh[i] += x[i];
+                }
+            }
         }
 #pragma unroll
         for (int m = 0; m < NC; ++m) stv<T, TV>(dc.f_nxt + kl + (size_t)c * rs + (size_t)m * nvp, out[m]);
-        constexpr int NR = M <= 4 ? 4 : 8;
-        T red[NR];
-#pragma unroll
-        for (int i = 0; i < NR; ++i) red[i] = i < M ? mom[i] : T(0);
-        const T sm = warp_transpose_sum<T, NR>(red);
+        double sm;
+        if constexpr (std::is_same<T, float>::value) sm = warp_transpose_sum_ff<NR>(mh, ml);
+        else sm = warp_transpose_sum<T, NR>(mh);
         const int vi = lane >> (NR == 4 ? 3 : 2);
         if ((lane & (NR == 4 ? 7 : 3)) == 0 && vi < M)
             dc.dW_part[((size_t)c * dc.n_vt + vt) * M + vi] = sm;
@@ -1547,11 +1633,14 @@ __device__ __forceinline__ void update_W_body(const DevCase<T> &dc, const int bx
     for (int m = 0; m < M; ++m) dsq[m] = wsq[m] = 0.0;
     if (c < dc.C) {
         double *Wc = dc.W + (size_t)c * M;
+        const bool counts = !dc.owned || dc.owned[c];      // halo cells of a subdomain do not count
         for (int m = 0; m < M; ++m) {
             double s = 0.0;
-            for (int t = 0; t < dc.n_vt; ++t) s += (double)dc.dW_part[((size_t)c * dc.n_vt + t) * M + m];
-            wsq[m] = Wc[m] * Wc[m];
-            dsq[m] = s * s;
+            for (int t = 0; t < dc.n_vt; ++t) s += dc.dW_part[((size_t)c * dc.n_vt + t) * M + m];
+            if (counts) {
+                wsq[m] = Wc[m] * Wc[m];
+                dsq[m] = s * s;
+            }
             Wc[m] += s;
         }
         Prim p = prim_of(Wc, D);
@@ -1563,7 +1652,9 @@ __device__ __forceinline__ void update_W_body(const DevCase<T> &dc, const int bx
         r[CR_LAM] = (T)p.lam;
         r[CR_PREF] = (T)pref_of(p.rho, p.lam, D);
         for (int d = 0; d < 3; ++d) r[CR_KQ + d] = d < D ? (T)(kappa * dc.q[(size_t)c * D + d]) : T(0);
-        r[CR_C] = (T)(0.5 * dc.dt / tau);
+        const double cc = 0.5 * dc.dt / tau;
+        r[CR_C] = (T)cc;
+        r[CR_INV] = (T)(1.0 / (1.0 + cc));
         r[CR_NB] = (T)(dc.nxi / (2.0 * p.lam));
         r[CR_NL2] = (T)(-p.lam * LOG2E);
     }
@@ -1635,12 +1726,11 @@ __device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx)
     if (c >= dc.C) return;
     const T *kr = dc.krec + (size_t)c * CREC;
     const T cc = kr[CR_C];
-    const T inv = T(1) / (T(1) + cc);
+    const T inv = kr[CR_INV];
     T U[D];
     for (int d = 0; d < D; ++d) U[d] = kr[CR_U + d];
     const size_t rs = (size_t)NC * dc.nvp;
-    T acc[D];
-    for (int d = 0; d < D; ++d) acc[d] = 0;
+    CSum<T> acc[D];
     for (int k0 = 4 * lane; k0 < dc.nvp; k0 += 128) {
         T ft[NC][4], fn[NC][4];
 #pragma unroll
@@ -1667,7 +1757,7 @@ __device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx)
             }
             const T we = dc.w[k] * (c2 * fn[0][j] + (NC == 2 ? fn[NC - 1][j] : T(0)));
 #pragma unroll
-            for (int d = 0; d < D; ++d) acc[d] += cv[d] * we;
+            for (int d = 0; d < D; ++d) acc[d].add(cv[d] * we);
         }
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
@@ -1680,8 +1770,8 @@ __device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx)
         }
     }
     for (int d = 0; d < D; ++d) {
-        T s = warp_sum(acc[d]);
-        if (lane == 0) dc.q[(size_t)c * D + d] = 0.5 * (double)s;
+        const double s = warp_sum(acc[d].value());
+        if (lane == 0) dc.q[(size_t)c * D + d] = 0.5 * s;
     }
 }
 
@@ -1772,6 +1862,41 @@ __global__ void k_check(const double *W, int n, int M, int *flags)
     if (bad) atomicOr(flags, 1);
 }
 
+// ------------------------------------------------------------ halo exchange
+// Rows of the halo buffer: f of the cell in the storage type [NC][nv], padded
+// to 8 bytes, then W [D+2] and q [D] in FP64.  One block per listed cell.
+template <typename T, int D, int NC>
+__global__ void k_halo_pack(DevCase<T> dc, const int *cells, int n, size_t row, unsigned char *buf)
+{
+    constexpr int M = D + 2;
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const int c = cells[i];
+    unsigned char *r = buf + (size_t)i * row;
+    T *fo = reinterpret_cast<T *>(r);
+    const T *fc = dc.f_cur + (size_t)c * NC * dc.nvp;
+    for (int j = threadIdx.x; j < NC * dc.nv; j += blockDim.x) fo[j] = fc[(size_t)(j / dc.nv) * dc.nvp + j % dc.nv];
+    double *tail = reinterpret_cast<double *>(r + row - (size_t)(M + D) * sizeof(double));
+    if (threadIdx.x < M) tail[threadIdx.x] = dc.W[(size_t)c * M + threadIdx.x];
+    else if (threadIdx.x < M + D) tail[threadIdx.x] = dc.q[(size_t)c * D + threadIdx.x - M];
+}
+
+template <typename T, int D, int NC>
+__global__ void k_halo_unpack(DevCase<T> dc, const int *cells, int n, size_t row, const unsigned char *buf)
+{
+    constexpr int M = D + 2;
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const int c = cells[i];
+    const unsigned char *r = buf + (size_t)i * row;
+    const T *fi = reinterpret_cast<const T *>(r);
+    T *fc = dc.f_cur + (size_t)c * NC * dc.nvp;
+    for (int j = threadIdx.x; j < NC * dc.nv; j += blockDim.x) fc[(size_t)(j / dc.nv) * dc.nvp + j % dc.nv] = fi[j];
+    const double *tail = reinterpret_cast<const double *>(r + row - (size_t)(M + D) * sizeof(double));
+    if (threadIdx.x < M) dc.W[(size_t)c * M + threadIdx.x] = tail[threadIdx.x];
+    else if (threadIdx.x < M + D) dc.q[(size_t)c * D + threadIdx.x - M] = tail[threadIdx.x];
+}
+
 // ------------------------------------------------------------ launchers
 static inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
 
@@ -1836,7 +1961,8 @@ template <typename T, int D>
 static size_t sk_smem(const DevCase<T> &dc, int k)
 {
     // k_face_sum1_sep: prefix sums of the last axis, 2 sides x 3 powers per warp
-    return k == SK_FACE_SUM1_SEP ? (size_t)SUM1_SEP_WARPS * 6 * (dc.cart_n[D - 1] + 1) * sizeof(T) : 0;
+    // (8-byte elements: FP64, or double-float pairs in the FP32 form)
+    return k == SK_FACE_SUM1_SEP ? (size_t)SUM1_SEP_WARPS * 6 * (dc.cart_n[D - 1] + 1) * 8 : 0;
 }
 
 // one per-case kernel, for one case (cases == nullptr) or for the cases of a
@@ -2078,6 +2204,25 @@ cudaError_t launch_f_import(const DevCase<T> &dc, const long long *perm, int c0,
     else k_f_import<T, 3, 1, S><<<cdiv(n, 256), 256, 0, st>>>(dc, perm, c0, nc, in);
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_halo(const DevCase<T> &dc, const int *cells, int n, size_t row, void *buf, int unpack,
+                        cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    if (dc.D == 2) {
+        if (unpack) k_halo_unpack<T, 2, 2><<<n, 128, 0, st>>>(dc, cells, n, row, (const unsigned char *)buf);
+        else k_halo_pack<T, 2, 2><<<n, 128, 0, st>>>(dc, cells, n, row, (unsigned char *)buf);
+    } else {
+        if (unpack) k_halo_unpack<T, 3, 1><<<n, 128, 0, st>>>(dc, cells, n, row, (const unsigned char *)buf);
+        else k_halo_pack<T, 3, 1><<<n, 128, 0, st>>>(dc, cells, n, row, (unsigned char *)buf);
+    }
+    return cudaGetLastError();
+}
+template cudaError_t launch_halo<double>(const DevCase<double> &, const int *, int, size_t, void *, int,
+                                         cudaStream_t);
+template cudaError_t launch_halo<float>(const DevCase<float> &, const int *, int, size_t, void *, int,
+                                        cudaStream_t);
 
 cudaError_t launch_residual(const double *res_part, int nblocks, int D, double *res, cudaStream_t st)
 {

@@ -48,6 +48,10 @@ cudaError_t launch_f_export(const DevCase<T> &dc, const long long *perm, int c0,
 template <typename T, typename S>
 cudaError_t launch_f_import(const DevCase<T> &dc, const long long *perm, int c0, int nc, const S *in, cudaStream_t st);
 cudaError_t launch_residual(const double *res_part, int nblocks, int D, double *res, cudaStream_t st);
+// halo rows of the listed internal cells to (unpack = 0) or from (1) a device buffer of n rows of `row` bytes
+template <typename T>
+cudaError_t launch_halo(const DevCase<T> &dc, const int *cells, int n, size_t row, void *buf, int unpack,
+                        cudaStream_t st);
 cudaError_t launch_moments_out(const double *W, const double *q, const long long *perm, int C, int D, double *out,
                                cudaStream_t st);
 cudaError_t launch_W_permute(const double *src, const long long *perm, int C, int D, double *dst, int to_internal,

@@ -10,6 +10,7 @@
 // sums in a fixed file-scope device array instead of allocated scratch.
 #include "../../include/ugks.h"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,7 +32,34 @@ static __device__ __align__(256) double g_res_scratch[kMaxBlocks * 2 * kMaxM];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-double *g_scratch_ptr[kMaxDevices] = {};
+// per device: the context in which the array's address was looked up, and the
+// address.  A new context on the device (after cudaDeviceReset, or a primary
+// context released and created again) maps the array elsewhere, so the address
+// is looked up again whenever the current context differs.
+struct ScratchSlot {
+    CUcontext ctx;
+    double *ptr;
+};
+ScratchSlot g_scratch[kMaxDevices] = {};
+
+// cuCtxGetCurrent through the runtime's driver entry point (the library links
+// only the CUDA runtime)
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+cudaError_t current_context(CUcontext *ctx)
+{
+    static std::once_flag once;
+    static CtxGetCurrentFn fn = nullptr;
+    static cudaError_t lookup = cudaSuccess;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSuccess;
+        lookup = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q);
+        if (lookup == cudaSuccess && q != cudaDriverEntryPointSuccess) lookup = cudaErrorSymbolNotFound;
+        fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    });
+    if (lookup != cudaSuccess) return lookup;
+    return fn(ctx) == CUDA_SUCCESS ? cudaSuccess : cudaErrorUnknown;
+}
 
 
 template <int M>
@@ -123,19 +151,28 @@ extern "C" ugks_status ugks_residual_noalloc(const double *W_old, const double *
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(UGKS_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(UGKS_EINVAL, "ugks_residual_noalloc: device index out of range");
+    CUcontext ctx = nullptr;
+    e = current_context(&ctx);
+    if (e != cudaSuccess) return fail(UGKS_ECUDA, std::string("cuCtxGetCurrent: ") + cudaGetErrorString(e));
     double *scratch = nullptr;
     {
-        // once per device, with that device current: the device address of the
-        // file-scope array (its name in host code is only a host-side stand-in)
+        // once per device and context, with that device current: the device
+        // address of the file-scope array (its name in host code is only a
+        // host-side stand-in).  The lookup makes the device's primary context
+        // current if none was, so the context is read again after it.
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_ptr[dev]) {
+        ScratchSlot &slot = g_scratch[dev];
+        if (!slot.ptr || !ctx || slot.ctx != ctx) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_res_scratch);
             if (e != cudaSuccess)
                 return fail(UGKS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_scratch_ptr[dev] = static_cast<double *>(p);
+            e = current_context(&ctx);
+            if (e != cudaSuccess) return fail(UGKS_ECUDA, std::string("cuCtxGetCurrent: ") + cudaGetErrorString(e));
+            slot.ctx = ctx;
+            slot.ptr = static_cast<double *>(p);
         }
-        scratch = g_scratch_ptr[dev];
+        scratch = slot.ptr;
     }
     const int nblocks = (int)((n_cells + kThreads - 1) / kThreads);
     cudaStream_t st = (cudaStream_t)stream;

@@ -64,3 +64,21 @@ def test_rejects_sizes_beyond_the_fixed_limit():
     p = ct.c_void_p(dummy.data_ptr())
     code = L.ugks_residual_noalloc(p, p, 2_097_153, 2, p, None)
     assert code == 1 and b"exceeds the fixed scratch limit" in L.ugks_last_error()
+
+
+def test_exactly_the_cell_limit_uses_the_last_scratch_row():
+    """At n_cells = 2,097,152 every row of the fixed scratch array holds a
+    block's partial sums.  The last cell carries most of the change, so a lost
+    or misplaced last block would change the result far beyond the tolerance.
+    Two calls in a row (3D, then 2D) against numpy on the same device arrays."""
+    n = 2_097_152
+    rng = np.random.default_rng(11)
+    for dim in (3, 2):
+        M = dim + 2
+        W_old = 1.0 + rng.random((n, M))
+        W_new = W_old + 1e-6 * rng.standard_normal((n, M))
+        W_new[-1] += 1.0
+        got = _noalloc_residual(W_old, W_new, dim)
+        d = W_new - W_old
+        ref = np.sqrt((d * d).sum(axis=0)) / np.sqrt((W_old * W_old).sum(axis=0))
+        assert np.allclose(got, ref, rtol=1e-10, atol=0), (dim, got, ref)
