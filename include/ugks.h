@@ -52,11 +52,12 @@ enum { UGKS_FACE_INTERIOR = 0, UGKS_FACE_WALL = 1, UGKS_FACE_FARFIELD = 2, UGKS_
 
 /* precision of the stored distribution and the per-velocity arithmetic.
  * UGKS_FP64: everything in FP64 (the plain method).
- * UGKS_FP32: f stored and streamed in FP32, per-velocity products in FP32;
- * every velocity-moment sum (interface W0 and the moments of g0, the wall
- * density, the heat flux, the moments of the flux residual that update W) is
- * accumulated with compensation per GPU lane (Kahan, or double-float) and
- * combined across lanes and velocity tiles in FP64; W, the equilibrium
+ * UGKS_FP32: f stored and streamed in FP32, per-velocity products in FP32,
+ * and every velocity-moment sum accumulated in FP64: the face sums (interface
+ * W0, the moments of g0) from FP32 partials of at most 16 terms per GPU lane
+ * (512 per warp), the wall density and the heat flux from Kahan-compensated
+ * FP32 lane sums, the moments of the flux residual that update W from
+ * double-float (about 44-bit) lane and warp sums; W, the equilibrium
  * parameters (rho, U, lambda), the heat flux and the collision coefficients
  * dt/(2 tau) and 1/(1 + dt/(2 tau)) are formed in FP64. */
 enum { UGKS_FP64 = 0, UGKS_FP32 = 1 };

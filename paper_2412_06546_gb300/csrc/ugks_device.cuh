@@ -47,10 +47,18 @@ constexpr int SUM1_SEP_MAX_NL = 512;
 // layout of the values of one gather entry (cell c, face f): a = LSQ
 // coefficient of the neighbour across f (0 for a wall), rs = x_f - x_c,
 // n = unit normal of f pointing out of c, ro = x_f - x_other (periodic image;
-// 0 for far-field ghosts), cs = -S_f / |Omega_c|
-template <int D> struct GEnt {
-    static constexpr int A = 0, RS = D, N = 2 * D, RO = 3 * D, CS = 4 * D;
-    static constexpr int LEN = (4 * D + 1 + 3) / 4 * 4;
+// 0 for far-field ghosts), cs = -S_f / |Omega_c|.  Grouped in 16-byte vectors
+// so that each pass loads only the vectors it reads: the slopes' first face
+// loop the first SLOPE1 values (a, rs), their limiter loop the first vector
+// (rs), the flux loop everything but the vectors in [SKIP0, SKIP1) (a, in 3D).
+template <int D> struct GEnt;
+template <> struct GEnt<2> {
+    static constexpr int A = 0, RS = 2, N = 4, RO = 6, CS = 8, LEN = 12;
+    static constexpr int SLOPE1 = 4, LIMIT = 4, SKIP0 = 0, SKIP1 = 0;
+};
+template <> struct GEnt<3> {
+    static constexpr int RS = 0, CS = 3, A = 4, N = 8, RO = 12, LEN = 16;
+    static constexpr int SLOPE1 = 8, LIMIT = 4, SKIP0 = 4, SKIP1 = 8;
 };
 
 // Everything a kernel needs, by value.  Geometry used inside velocity loops is
@@ -66,6 +74,7 @@ struct DevCase {
     // velocity grid (padded), FP64 and T copies
     const double *ud[3], *wd;
     const T *u[3], *w;
+    const T *uw;                  // [nvp][4] (u_x, u_y, u_z or 0, w) packed for one vector load
     // distribution: f_cur = f^n, f_nxt = f~ written by the gather pass
     T *f_cur, *f_nxt;
     // macroscopic state
@@ -120,7 +129,7 @@ struct DevCase {
     double *fsum1, *fsum2;        // [F][S1], [F][S2]
     double *fprim0;               // [F][D+2] rho0, U0, lam0
     double *fqs;                  // [F][5] time integrals q1..q5 of the interface
-    double *dW_part;              // [C][n_vt][D+2] moments of the flux residual over one velocity tile
+    double *dW_part;              // [C][n_groups][D+2] moments of the flux residual over a tile group
     double *res_part;             // [n_res_blocks][2(D+2)]
     const unsigned char *owned;   // [C] 1 for cells whose residual counts (a subdomain's own cells),
                                   // nullptr: every cell
@@ -133,7 +142,8 @@ struct DevCase {
     // gather tiling
     int P, n_patches, n_vt, vtile;
     int nth;                      // threads per gather CTA (256, or 512 for FP32 at TV <= 2)
-    int vt_group;                 // gather grid order: groups of vt_group velocity tiles (see k_gather)
+    int vt_group;                 // velocity tiles per gather CTA (see k_gather)
+    int n_groups;                 // tile groups: ceil(n_vt / vt_group)
     const int *ring_ptr, *ring_cells;
 };
 
@@ -214,6 +224,16 @@ template <> struct CSum<float> {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// Blocked accumulation in FP64 for sums with many terms per lane and many
+// values (the face sums): every lane adds at most SUM_BLOCK of its FP32 terms
+// per value into blk[] (a block of 32 x SUM_BLOCK terms per warp), the warp
+// combines each block value across lanes (warp_transpose_sum, FP32), and the
+// block totals are accumulated in FP64, lane j holding value j >> (5 - log2 N).
+// The FP32 part of every sum spans one block, so its rounding error is bounded
+// by about (SUM_BLOCK + 5) units in the last place of the block's absolute sum
+// whatever the number of terms.
+constexpr int SUM_BLOCK = 16;
+
 // Error-free sum of two FP32 values (Knuth's TwoSum): a + b = s + e exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -234,10 +254,10 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float bh, float bl)
 }
 
 // warp_transpose_sum on double-float pairs (h, l): the same exchange pattern,
-// with every addition a double-float addition.  Returns the full sum of value
-// index lane >> (5 - log2 N) as hi + lo in FP64.
+// with every addition a double-float addition.  On return (oh, ol) is the
+// full sum of value index lane >> (5 - log2 N).
 template <int N>
-__device__ __forceinline__ double warp_transpose_sum_ff(float (&h)[N], float (&l)[N])
+__device__ __forceinline__ void warp_transpose_sum_ff2(float (&h)[N], float (&l)[N], float &oh, float &ol)
 {
     const int lane = threadIdx.x & 31;
     int n = N;
@@ -256,20 +276,22 @@ __device__ __forceinline__ double warp_transpose_sum_ff(float (&h)[N], float (&l
             ff_add(h[i], l[i], rh, rl);
         }
     }
-    constexpr int used = (N == 8) ? 3 : (N == 4 ? 2 : (N == 2 ? 1 : 0));
+    constexpr int used = (N == 32) ? 5 : (N == 16) ? 4 : (N == 8) ? 3 : (N == 4 ? 2 : (N == 2 ? 1 : 0));
     float rh = h[0], rl = l[0];
 #pragma unroll
     for (int bit = 16 >> used; bit > 0; bit >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, rh, bit), ol = __shfl_xor_sync(0xffffffffu, rl, bit);
-        ff_add(rh, rl, oh, ol);
+        const float qh = __shfl_xor_sync(0xffffffffu, rh, bit), ql = __shfl_xor_sync(0xffffffffu, rl, bit);
+        ff_add(rh, rl, qh, ql);
     }
-    return (double)rh + (double)rl;
+    oh = rh;
+    ol = rl;
 }
 
-// Sum of N (4 or 8) values over the 32 lanes of a warp by recursive halving:
-// at every exchange a lane keeps half of its values and receives the
-// partner's partial sums of that half.  On return lane l holds the full sum
-// of value index l >> (5 - log2 N) (lanes 8j..8j+7 for N = 4).
+// Sum of N (a power of two up to 32) values over the 32 lanes of a warp by
+// recursive halving: at every exchange a lane keeps half of its values and
+// receives the partner's partial sums of that half.  On return lane l holds
+// the full sum of value index l >> (5 - log2 N) (lanes 8j..8j+7 for N = 4,
+// lane j for N = 32).
 template <typename T, int N>
 __device__ __forceinline__ T warp_transpose_sum(T (&v)[N])
 {
@@ -287,11 +309,19 @@ __device__ __forceinline__ T warp_transpose_sum(T (&v)[N])
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
         }
     }
-    constexpr int used = (N == 8) ? 3 : (N == 4 ? 2 : (N == 2 ? 1 : 0));
+    constexpr int used = (N == 32) ? 5 : (N == 16) ? 4 : (N == 8) ? 3 : (N == 4 ? 2 : (N == 2 ? 1 : 0));
+    static_assert((1 << used) == N, "N must be a power of two up to 32");
     T r = v[0];
 #pragma unroll
     for (int bit = 16 >> used; bit > 0; bit >>= 1) r += __shfl_xor_sync(0xffffffffu, r, bit);
     return r;
+}
+
+// the block step of the blocked FP64 accumulation (see SUM_BLOCK)
+template <int N>
+__device__ __forceinline__ double block_to_fp64(float (&blk)[N])
+{
+    return (double)warp_transpose_sum<float, N>(blk);
 }
 
 // Maxwellian H and the b-factor of a record (cell / ghost / side / wall)
@@ -403,6 +433,26 @@ __device__ __forceinline__ void load_rec(const double *__restrict__ p, double (&
     }
 }
 
+// velocity k and its weight from the packed array, one 16-byte (FP32) or two
+// 16-byte (FP64) loads
+__device__ __forceinline__ void load_uw(const float *__restrict__ uw, int k, float u[3], float &w)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(uw) + k);
+    u[0] = v.x;
+    u[1] = v.y;
+    u[2] = v.z;
+    w = v.w;
+}
+__device__ __forceinline__ void load_uw(const double *__restrict__ uw, int k, double u[3], double &w)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(uw) + 2 * k);
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(uw) + 2 * k + 1);
+    u[0] = a.x;
+    u[1] = a.y;
+    u[2] = b.x;
+    w = b.y;
+}
+
 // Micro reconstruction of cell c at velocity index k (Sec. 3.1 Step 2):
 // least-squares slope grad = sum_j a_cj (f_j - f_c), Venkatakrishnan factor
 // phi = min over the faces of c of (D1^2 + eps^2 + 2 D1 D2) / (D1^2 + 2 D2^2 +
@@ -449,12 +499,10 @@ __device__ __forceinline__ void cell_slope(const DevCase<T> &dc, const T *__rest
         }
     }
     const T e2 = dc.eps2[c];
-    T phi[NC], dmin[NC];
+    // the limiter at the extreme d2 only (see cell_slope_tv)
+    T phi[NC], dmin[NC], dmax[NC];
 #pragma unroll
-    for (int m = 0; m < NC; ++m) {
-        phi[m] = T(1);
-        dmin[m] = T(0);
-    }
+    for (int m = 0; m < NC; ++m) dmin[m] = dmax[m] = T(0);
     const int s0 = dc.cf_ptr[c], s1 = dc.cf_ptr[c + 1];
     for (int s = s0; s < s1; ++s) {
         T r[D];
@@ -466,12 +514,25 @@ __device__ __forceinline__ void cell_slope(const DevCase<T> &dc, const T *__rest
 #pragma unroll
             for (int d = 0; d < D; ++d) d2 += g[m][d] * r[d];
             dmin[m] = d2 < dmin[m] ? d2 : dmin[m];
-            if (dc.limiter) {
-                T d1 = d2 > T(0) ? vmax[m] - fi[m] : vmin[m] - fi[m];
-                T a2 = d1 * d1 + e2;
-                T num = a2 + T(2) * d1 * d2;
-                T den = a2 + d2 * (T(2) * d2 + d1);
-                T ph = den > T(0) ? fdiv(num, den) : T(1);
+            dmax[m] = d2 > dmax[m] ? d2 : dmax[m];
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+        phi[m] = T(1);
+        if (dc.limiter) {
+            auto venk = [&](T d1, T d2) {
+                const T a2 = d1 * d1 + e2;
+                const T num = a2 + T(2) * d1 * d2;
+                const T den = a2 + d2 * (T(2) * d2 + d1);
+                return den > T(0) ? fdiv(num, den) : T(1);
+            };
+            if (dmax[m] > T(0)) {
+                const T ph = venk(vmax[m] - fi[m], dmax[m]);
+                phi[m] = ph < phi[m] ? ph : phi[m];
+            }
+            if (dmin[m] < T(0)) {
+                const T ph = venk(vmin[m] - fi[m], dmin[m]);
                 phi[m] = ph < phi[m] ? ph : phi[m];
             }
         }
@@ -501,7 +562,7 @@ __device__ __forceinline__ void cell_slope_tv(const DevCase<T> &dc, const T *__r
                                               const T (&u)[3][TV], T (&g)[NC][D][TV], T (&fi)[NC][TV])
 {
     using E = GEnt<D>;
-    constexpr int HA = (2 * D + 3) / 4 * 4;       // a and rs, rounded to whole vector loads
+    constexpr int HA = E::SLOPE1;                 // a and rs, in whole vector loads
     const int nvp = dc.nvp;
     const size_t rs = (size_t)NC * nvp;
     T vmax[NC][TV], vmin[NC][TV];
@@ -551,18 +612,21 @@ __device__ __forceinline__ void cell_slope_tv(const DevCase<T> &dc, const T *__r
             }
     }
     const T e2 = __ldg(dc.eps2 + c);
-    T phi[NC][TV], dmin[NC][TV];
+    // Venkatakrishnan's factor at a face, phi(d2) = (a2 + 2 d1 d2) / (a2 + d2 (2 d2 + d1))
+    // with a2 = d1^2 + eps^2 and d1 of the sign of d2, is at least 1 for
+    // 0 <= d2/d1 <= 1/2 and strictly decreasing in |d2| beyond.  Its minimum over
+    // the faces (clipped at 1) is therefore taken at the largest and at the most
+    // negative d2, so the face loop only tracks those two, and phi is evaluated
+    // twice per velocity instead of once per face.
+    T dmax[NC][TV], dmin[NC][TV];
 #pragma unroll
     for (int m = 0; m < NC; ++m)
 #pragma unroll
-        for (int j = 0; j < TV; ++j) {
-            phi[m][j] = T(1);
-            dmin[m][j] = T(0);
-        }
+        for (int j = 0; j < TV; ++j) dmax[m][j] = dmin[m][j] = T(0);
 #pragma unroll 4
     for (int e = e0; e < e1; ++e) {
-        T ge[HA];
-        load_rec<HA>(dc.gf + (size_t)e * E::LEN, ge);
+        T ge[E::LIMIT];
+        load_rec<E::LIMIT>(dc.gf + (size_t)e * E::LEN, ge);
 #pragma unroll
         for (int m = 0; m < NC; ++m)
 #pragma unroll
@@ -571,16 +635,32 @@ __device__ __forceinline__ void cell_slope_tv(const DevCase<T> &dc, const T *__r
 #pragma unroll
                 for (int d = 0; d < D; ++d) d2 += g[m][d][j] * ge[E::RS + d];
                 dmin[m][j] = d2 < dmin[m][j] ? d2 : dmin[m][j];
-                if (dc.limiter) {
-                    const T d1 = d2 > T(0) ? vmax[m][j] - fi[m][j] : vmin[m][j] - fi[m][j];
+                dmax[m][j] = d2 > dmax[m][j] ? d2 : dmax[m][j];
+            }
+    }
+    T phi[NC][TV];
+#pragma unroll
+    for (int m = 0; m < NC; ++m)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+            phi[m][j] = T(1);
+            if (dc.limiter) {
+                auto venk = [&](T d1, T d2) {
                     const T a2 = d1 * d1 + e2;
                     const T num = a2 + T(2) * d1 * d2;
                     const T den = a2 + d2 * (T(2) * d2 + d1);
-                    const T ph = den > T(0) ? fdiv(num, den) : T(1);
+                    return den > T(0) ? fdiv(num, den) : T(1);
+                };
+                if (dmax[m][j] > T(0)) {
+                    const T ph = venk(vmax[m][j] - fi[m][j], dmax[m][j]);
+                    phi[m][j] = ph < phi[m][j] ? ph : phi[m][j];
+                }
+                if (dmin[m][j] < T(0)) {
+                    const T ph = venk(vmin[m][j] - fi[m][j], dmin[m][j]);
                     phi[m][j] = ph < phi[m][j] ? ph : phi[m][j];
                 }
             }
-    }
+        }
     const T dt = dc.dtT;
 #pragma unroll
     for (int m = 0; m < NC; ++m)

@@ -60,7 +60,7 @@ struct ugks_case {
     ugks::DevCase<double> d64{};
     ugks::DevCase<float> d32{};
     ugks::StepConfig cfg{};
-    int P = 0, vtile = 0, nth = 256, n_patches = 0, n_vt = 0, vt_group = 1;
+    int P = 0, vtile = 0, nth = 256, n_patches = 0, n_vt = 0, vt_group = 1, n_groups = 1;
     long long *perm_d = nullptr;   // caller cell i -> internal cell
     std::vector<long long> perm_h; // the same on the host
     std::vector<long long> wall_face_h;   // face id of every wall slot
@@ -471,17 +471,22 @@ void preprocess(const ugks_mesh *m, const ugks_params *p, int P, Host &h)
             const int f = h.cf_face[e], t = h.ftype[f];
             const bool own = h.cf_side[e] == 0;
             double *g = &h.gf[(size_t)e * GL];
+            const int oA = D == 2 ? ugks::GEnt<2>::A : ugks::GEnt<3>::A;
+            const int oRS = D == 2 ? ugks::GEnt<2>::RS : ugks::GEnt<3>::RS;
+            const int oN = D == 2 ? ugks::GEnt<2>::N : ugks::GEnt<3>::N;
+            const int oRO = D == 2 ? ugks::GEnt<2>::RO : ugks::GEnt<3>::RO;
+            const int oCS = D == 2 ? ugks::GEnt<2>::CS : ugks::GEnt<3>::CS;
             if (t != UGKS_FACE_WALL) {
-                for (int d = 0; d < D; ++d) g[d] = h.nb_a[(size_t)q * D + d];
+                for (int d = 0; d < D; ++d) g[oA + d] = h.nb_a[(size_t)q * D + d];
                 ++q;
             }
             for (int d = 0; d < D; ++d) {
-                g[D + d] = h.cf_r[(size_t)e * D + d];
-                g[2 * D + d] = own ? h.fn[(size_t)f * D + d] : -h.fn[(size_t)f * D + d];
+                g[oRS + d] = h.cf_r[(size_t)e * D + d];
+                g[oN + d] = own ? h.fn[(size_t)f * D + d] : -h.fn[(size_t)f * D + d];
                 if (t == UGKS_FACE_INTERIOR || t == UGKS_FACE_PERIODIC)
-                    g[3 * D + d] = own ? h.frR[(size_t)f * D + d] : h.frL[(size_t)f * D + d];
+                    g[oRO + d] = own ? h.frR[(size_t)f * D + d] : h.frL[(size_t)f * D + d];
             }
-            g[4 * D] = -m->face_S[f] / h.vol[c];
+            g[oCS] = -m->face_S[f] / h.vol[c];
         }
     }
 
@@ -640,6 +645,14 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     for (int64_t k = 0; k < c->Nv; ++k) wd[k] = v->w[k];
     dc.wd = c->upload(wd);
     dc.w = c->upload(cast<T>(wd));
+    {
+        std::vector<T> uw((size_t)c->nvp * 4, T(0));
+        for (int64_t k = 0; k < c->Nv; ++k) {
+            for (int d = 0; d < D; ++d) uw[(size_t)k * 4 + d] = (T)v->u[k * D + d];
+            uw[(size_t)k * 4 + 3] = (T)v->w[k];
+        }
+        dc.uw = c->upload(uw);
+    }
     // state
     const size_t fcount = (size_t)c->C * c->NC * c->nvp;
     dc.f_cur = (T *)c->dalloc(fcount * sizeof(T));
@@ -750,6 +763,7 @@ void fill_case(ugks_case *c, ugks::DevCase<T> &dc, const ugks_mesh *m, const ugk
     dc.P = c->P;
     dc.nth = c->nth;
     dc.vt_group = c->vt_group;
+    dc.n_groups = c->n_groups;
     dc.n_patches = c->n_patches;
     dc.n_vt = c->n_vt;
     dc.vtile = c->vtile;
@@ -772,6 +786,13 @@ struct Tiling {
 std::mutex g_tune_mutex;
 std::map<std::string, Tiling> g_tune_cache;
 
+// dynamic shared memory of the gather: the moment accumulators (P x 16
+// values) and the slope buffer ((patch + ring) x NC x D x vtile values)
+size_t gather_smem(int max_slope, int NC, int D, int vtile, int P, size_t esz)
+{
+    return ((size_t)P * 16 + (size_t)max_slope * NC * D * vtile) * esz;
+}
+
 // velocity tile used when neither the caller nor the autotuner sets one
 int kDefaultVtile(int prec) { return prec == UGKS_FP64 ? 32 : 64; }
 
@@ -784,6 +805,7 @@ void set_tiling(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, int vt
     c->nth = nth;
     c->n_vt = (int)(c->nvp / vtile);
     c->vt_group = std::max(1, std::min(G, c->n_vt));
+    c->n_groups = (c->n_vt + c->vt_group - 1) / c->vt_group;
     c->cfg.smem = smem;
     dc.P = P;
     dc.n_patches = c->n_patches;
@@ -791,6 +813,7 @@ void set_tiling(ugks_case *c, ugks::DevCase<T> &dc, const Host &h, int P, int vt
     dc.nth = nth;
     dc.n_vt = c->n_vt;
     dc.vt_group = c->vt_group;
+    dc.n_groups = c->n_groups;
     // the old patch arrays may still be read by queued kernels: drain the
     // stream first, so that any allocator may reuse them at once
     if (dc.ring_ptr || dc.ring_cells || dc.gi)
@@ -819,12 +842,12 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
         if (it != g_tune_cache.end()) best = it->second;
     }
     const int C = (int)c->C;
-    auto smem_of = [&](const Host &hh, int vt) { return (size_t)hh.max_slope * c->NC * c->D * vt * esz; };
+    auto smem_of = [&](const Host &hh, int vt, int P) { return gather_smem(hh.max_slope, c->NC, c->D, vt, P, esz); };
     if (best.P == 0) {
         // tetrahedra have more faces and larger rings than triangles, and one
         // stored component per velocity: smaller patches and wider velocity tiles
         const std::vector<int> pc = c->prec == UGKS_FP64 ? std::vector<int>{16, 24, 32, 48}
-                                    : c->D == 3          ? std::vector<int>{12, 16, 24, 32, 48}
+                                    : c->D == 3          ? std::vector<int>{16, 24, 32, 48, 64, 96}
                                                          : std::vector<int>{24, 32, 48, 64, 96};
         std::vector<int> vc = {c->vtile};
         if (tune_vtile) vc = c->D == 3 ? std::vector<int>{32, 64, 128} : std::vector<int>{32, 64};
@@ -854,7 +877,7 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
                     if (P > C && P != pc.front()) continue;
                     if (nth == 512 && P < 32) continue;          // 16 warps need work
                     build_patches(h, C, P);
-                    const size_t smem = smem_of(h, vt);
+                    const size_t smem = smem_of(h, vt, P);
                     if (smem > (size_t)smem_max) continue;
                     set_tiling(c, dc, h, P, vt, nth, G0, smem);
                     const float ms = time_gather(smem);
@@ -867,11 +890,12 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
         // then the grid order at the chosen tiling: groups of G velocity tiles
         if (best.P != 0 && tune_group) {
             build_patches(h, C, best.P);
-            const size_t smem = smem_of(h, best.vtile);
+            const size_t smem = smem_of(h, best.vtile, best.P);
             set_tiling(c, dc, h, best.P, best.vtile, best.nth, G0, smem);
-            for (int G : {1, 2, 4, 8, 16, 32}) {
+            for (int G : {1, 2, 4, 8, 16, 32, 64}) {
                 if (G == G0 || G > c->n_vt) continue;
                 dc.vt_group = G;
+                dc.n_groups = (c->n_vt + G - 1) / G;
                 const float ms = time_gather(smem);
                 if (ms < best_ms) {
                     best.G = G;
@@ -879,6 +903,7 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
                 }
             }
             dc.vt_group = c->vt_group;
+            dc.n_groups = c->n_groups;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -888,10 +913,11 @@ void autotune(ugks_case *c, ugks::DevCase<T> &dc, Host &h, int smem_max, bool tu
     }
     if (best.P != c->P || best.vtile != c->vtile || best.nth != c->nth) {
         build_patches(h, C, best.P);
-        const size_t smem = smem_of(h, best.vtile);
+        const size_t smem = smem_of(h, best.vtile, best.P);
         if (smem <= (size_t)smem_max) set_tiling(c, dc, h, best.P, best.vtile, best.nth, best.G, smem);
     } else if (best.G != c->vt_group) {
         c->vt_group = dc.vt_group = best.G;
+        c->n_groups = dc.n_groups = (c->n_vt + best.G - 1) / best.G;
     }
 }
 
@@ -1073,7 +1099,7 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         for (;;) {
             h = Host();
             preprocess(mesh, params, P, h);
-            const size_t smem = (size_t)h.max_slope * c->NC * c->D * c->vtile * esz;
+            const size_t smem = gather_smem(h.max_slope, c->NC, c->D, c->vtile, P, esz);
             if (smem <= (size_t)smem_max || P <= 4) {
                 if (smem > (size_t)smem_max) fail(UGKS_EINVAL, "mesh stencil too large for shared memory");
                 c->cfg.smem = smem;
@@ -1086,6 +1112,7 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         c->nvp = (c->Nv + vpad - 1) / vpad * vpad;
         c->n_vt = (int)(c->nvp / c->vtile);
         c->vt_group = std::max(1, std::min(params->gather_tile_group > 0 ? params->gather_tile_group : 1, c->n_vt));
+        c->n_groups = (c->n_vt + c->vt_group - 1) / c->vt_group;
         c->G = (int)h.gface.size();
         c->NW = (int)h.wface.size();
         // upwind CFL bound (the CFL step of Algorithm 1)
@@ -1509,18 +1536,18 @@ void batch_build(ugks_batch *b)
         g.vtile = vtile;
         g.nth = nth;
         std::vector<int4> work;
-        int max_vt = 0;
+        int max_grp = 0;
         for (int i = 0; i < n; ++i)
             if (in_group(b->cases[i])) {
                 g.smem = std::max(g.smem, b->cases[i]->cfg.smem);
-                max_vt = std::max(max_vt, b->cases[i]->n_vt);
+                max_grp = std::max(max_grp, b->cases[i]->n_groups);
             }
-        // velocity tile outer, case, then patch innermost: consecutive CTAs work
-        // on neighbouring patches of one case and tile, as in the single-case grid
-        for (int vt = 0; vt < max_vt; ++vt)
+        // tile group outer, case, then patch innermost: consecutive CTAs work
+        // on neighbouring patches of one case and group, as in the single-case grid
+        for (int gr = 0; gr < max_grp; ++gr)
             for (int i = 0; i < n; ++i) {
-                if (!in_group(b->cases[i]) || vt >= b->cases[i]->n_vt) continue;
-                for (int pi = 0; pi < b->cases[i]->n_patches; ++pi) work.push_back(make_int4(i, pi, vt, 0));
+                if (!in_group(b->cases[i]) || gr >= b->cases[i]->n_groups) continue;
+                for (int pi = 0; pi < b->cases[i]->n_patches; ++pi) work.push_back(make_int4(i, pi, gr, 0));
             }
         cuda_ok(cudaMalloc((void **)&g.work, sizeof(int4) * std::max<size_t>(1, work.size())), "batch alloc");
         b->groups.push_back(g);      // owned by the batch from here on

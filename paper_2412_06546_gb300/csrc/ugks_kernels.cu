@@ -14,11 +14,13 @@
 //   k_update_W    W^{n+1} and stage-2 coefficients                       (Eq. macroscopicUpdata)
 //   k_collide     stage 2 and the heat flux of f^{n+1}                   (Eq. microS2)
 // All per-velocity arithmetic is in T (double or float).  Velocity-moment sums
-// are FP64 in the FP64 form; in the FP32 form each lane's terms are summed with
-// compensation (Kahan, or double-float in the gather's residual moments and the
-// separable prefix sums) and the lanes are combined in FP64.  Macroscopic
-// scalars (W, the equilibrium parameters, the heat flux, the collision
-// coefficients) are formed in FP64.
+// are FP64 in the FP64 form.  In the FP32 form the products are FP32 and the
+// sums are accumulated in FP64: the face sums from FP32 block partials of at
+// most SUM_BLOCK terms per lane (see block_to_fp64), the wall density and the
+// heat flux from Kahan-compensated lane sums, the moments of the flux residual
+// from double-float lane and warp sums.  Macroscopic scalars (W, the
+// equilibrium parameters, the heat flux, the collision coefficients) are
+// formed in FP64.
 #include "ugks_device.cuh"
 #include "ugks_kernels.h"
 
@@ -466,9 +468,6 @@ __global__ void k_face_pre_batch(const DevCase<T> *__restrict__ cases, const int
     face_pre_body<T, D, NC>(dc, bx);
 }
 
-// terms per lane that the FP32 face sums add directly before compensating
-constexpr int SUM_BLOCK = 4;
-
 // half-range moments: sum_k w psi_c [H(u_n) g_L + (1 - H(u_n)) g_R], centred at U_ref
 template <typename T, int D, int NC>
 __device__ __forceinline__ void face_sum1_body(const DevCase<T> &dc, const int bx)
@@ -484,48 +483,59 @@ __device__ __forceinline__ void face_sum1_body(const DevCase<T> &dc, const int b
         n[d] = dc.fn[(size_t)f * D + d];
         Ur[d] = (T)dc.fUref[(size_t)f * D + d];
     }
-    // FP32 form: blocks of SUM_BLOCK terms of a lane are summed directly, the
-    // block sums compensated (CSum), the lanes combined in FP64
-    constexpr int B = std::is_same<T, float>::value ? SUM_BLOCK : 1;
-    CSum<T> acc[M];
-    for (int k0 = lane; k0 < dc.nvp; k0 += 32 * B) {
-        T blk[M];
-#pragma unroll
-        for (int m = 0; m < M; ++m) blk[m] = 0;
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            const int k = k0 + 32 * j;
-            if (B > 1 && k >= dc.nvp) break;
-            T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
-            T un = normal_velocity<T, D>(u, n);
-            T h, b;
-            if (un != T(0)) {
-                const T *s = un > T(0) ? sL : sR;
-                h = maxwell_h<T, D>(s, u);
-                b = s[GR_NB] * h;
-            } else {
-                T hl = maxwell_h<T, D>(sL, u), hr = maxwell_h<T, D>(sR, u);
-                h = T(0.5) * hl + T(0.5) * hr;
-                b = T(0.5) * sL[GR_NB] * hl + T(0.5) * sR[GR_NB] * hr;
-            }
-            T wk = dc.w[k];
-            T c2 = 0;
-            T wh = wk * h;
-            blk[0] += wh;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                T c = u[d] - Ur[d];
-                c2 += c * c;
-                blk[1 + d] += c * wh;
-            }
-            blk[D + 1] += T(0.5) * wk * (c2 * h + b);
+    // the terms of velocity k, added into a[0..M)
+    auto terms = [&](int k, T *a) {
+        T u[3], wk;
+        load_uw(dc.uw, k, u, wk);
+        T un = normal_velocity<T, D>(u, n);
+        T h, b;
+        if (un != T(0)) {
+            const T *s = un > T(0) ? sL : sR;
+            h = maxwell_h<T, D>(s, u);
+            b = s[GR_NB] * h;
+        } else {
+            T hl = maxwell_h<T, D>(sL, u), hr = maxwell_h<T, D>(sR, u);
+            h = T(0.5) * hl + T(0.5) * hr;
+            b = T(0.5) * sL[GR_NB] * hl + T(0.5) * sR[GR_NB] * hr;
         }
+        T c2 = 0;
+        T wh = wk * h;
+        a[0] += wh;
 #pragma unroll
-        for (int m = 0; m < M; ++m) acc[m].add(blk[m]);
-    }
-    for (int m = 0; m < M; ++m) {
-        const double s = warp_sum(acc[m].value());
-        if (lane == 0) dc.fsum1[(size_t)f * M + m] = s;
+        for (int d = 0; d < D; ++d) {
+            T c = u[d] - Ur[d];
+            c2 += c * c;
+            a[1 + d] += c * wh;
+        }
+        a[D + 1] += T(0.5) * wk * (c2 * h + b);
+    };
+    if constexpr (std::is_same<T, float>::value) {
+        // blocked sums accumulated in FP64 (SUM_BLOCK terms per lane per block)
+        constexpr int NP = M <= 4 ? 4 : 8;
+        double acc = 0.0;
+        for (int k0 = lane; k0 < dc.nvp; k0 += 32 * SUM_BLOCK) {
+            float blk[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) blk[i] = 0.f;
+#pragma unroll 4
+            for (int j = 0; j < SUM_BLOCK; ++j) {
+                const int k = k0 + 32 * j;
+                if (k >= dc.nvp) break;              // uniform: nvp is a multiple of 32
+                terms(k, blk);
+            }
+            acc += block_to_fp64<NP>(blk);
+        }
+        const int vi = lane >> (NP == 4 ? 3 : 2);
+        if ((lane & (NP == 4 ? 7 : 3)) == 0 && vi < M) dc.fsum1[(size_t)f * M + vi] = acc;
+    } else {
+        T acc[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc[m] = 0;
+        for (int k = lane; k < dc.nvp; k += 32) terms(k, acc);
+        for (int m = 0; m < M; ++m) {
+            const double sm = warp_sum(acc[m]);
+            if (lane == 0) dc.fsum1[(size_t)f * M + m] = sm;
+        }
     }
 }
 
@@ -554,59 +564,18 @@ __global__ void k_face_sum1_batch(const DevCase<T> *__restrict__ cases, const in
 // (NL + 1) doubles per warp.
 constexpr int SUM1_SEP_WARPS = 4;
 
-// Prefix-sum element of k_face_sum1_sep: FP64 in the FP64 form, a
-// double-float pair (hi, lo) in the FP32 form, so that the range sums, which
-// are differences of prefix sums, keep about 44 significant bits.
-template <typename T> struct PSum;
-template <> struct PSum<double> {
-    using type = double;
-    static __device__ __forceinline__ double make(double x) { return x; }
-    static __device__ __forceinline__ void add(double &a, double b) { a += b; }
-    static __device__ __forceinline__ double shfl_up(double a, int o) { return __shfl_up_sync(0xffffffffu, a, o); }
-    static __device__ __forceinline__ double shfl(double a, int l) { return __shfl_sync(0xffffffffu, a, l); }
-    // (a1 - a0) + (b1 - b0) / 2
-    static __device__ __forceinline__ double range(double a1, double a0, double b1, double b0)
-    {
-        return (a1 - a0) + 0.5 * (b1 - b0);
-    }
-};
-template <> struct PSum<float> {
-    using type = float2;
-    static __device__ __forceinline__ float2 make(float x) { return make_float2(x, 0.f); }
-    static __device__ __forceinline__ void add(float2 &a, float2 b) { ff_add(a.x, a.y, b.x, b.y); }
-    static __device__ __forceinline__ float2 shfl_up(float2 a, int o)
-    {
-        return make_float2(__shfl_up_sync(0xffffffffu, a.x, o), __shfl_up_sync(0xffffffffu, a.y, o));
-    }
-    static __device__ __forceinline__ float2 shfl(float2 a, int l)
-    {
-        return make_float2(__shfl_sync(0xffffffffu, a.x, l), __shfl_sync(0xffffffffu, a.y, l));
-    }
-    static __device__ __forceinline__ float range(float2 a1, float2 a0, float2 b1, float2 b0)
-    {
-        float h = a1.x, l = a1.y;
-        ff_add(h, l, -a0.x, -a0.y);
-        float bh = b1.x, bl = b1.y;
-        ff_add(bh, bl, -b0.x, -b0.y);
-        ff_add(h, l, 0.5f * bh, 0.5f * bl);
-        return __fadd_rn(h, l);
-    }
-};
-
 template <typename T, int D, int NC>
 __device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const int bx)
 {
-    using PS = PSum<T>;
-    using E = typename PS::type;
     extern __shared__ __align__(16) unsigned char psum_raw[];
-    E *psum = reinterpret_cast<E *>(psum_raw);
+    T *psum = reinterpret_cast<T *>(psum_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int f = bx * SUM1_SEP_WARPS + warp;
     constexpr int M = D + 2;
     constexpr int L = D - 1;                 // the prefix-sum axis
     const int NL = dc.cart_n[L];
     if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
-    E *P = psum + (size_t)warp * 6 * (NL + 1);
+    T *P = psum + (size_t)warp * 6 * (NL + 1);
     const T *side[2] = {dc.fside + (size_t)f * 2 * GREC, dc.fside + (size_t)f * 2 * GREC + GREC};
     T n[D], Ur[D];
     for (int d = 0; d < D; ++d) {
@@ -614,35 +583,34 @@ __device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const i
         Ur[d] = (T)dc.fUref[(size_t)f * D + d];
     }
     // prefix sums over the last axis of w g (u - Ur)^p, p = 0, 1, 2, per side
+    // (at most SUM1_SEP_MAX_NL = 512 terms each: one block of the FP32 form's
+    // blocked sums)
     for (int s = 0; s < 2; ++s) {
         const T *r = side[s];
-        E *Ps = P + s * 3 * (NL + 1);
-        if (lane == 0) Ps[0] = Ps[NL + 1] = Ps[2 * (NL + 1)] = PS::make(T(0));
-        E carry[3] = {PS::make(T(0)), PS::make(T(0)), PS::make(T(0))};
+        T *Ps = P + s * 3 * (NL + 1);
+        if (lane == 0) Ps[0] = Ps[NL + 1] = Ps[2 * (NL + 1)] = T(0);
+        T carry[3] = {0, 0, 0};
         for (int j0 = 0; j0 < NL; j0 += 32) {
             const int j = j0 + lane;
-            T x[3] = {0, 0, 0};
+            T v[3] = {0, 0, 0};
             if (j < NL) {
                 const T a = dc.axis[L][j];
                 const T dv = a - r[GR_U + L];
                 const T g = dc.axw[L][j] * gauss<T>(r[GR_LAM], r[GR_NL2], dv * dv);
                 const T c = a - Ur[L];
-                x[0] = g;
-                x[1] = g * c;
-                x[2] = g * c * c;
+                v[0] = g;
+                v[1] = g * c;
+                v[2] = g * c * c;
             }
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
-                E v = PS::make(x[p]);
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const E t = PS::shfl_up(v, o);
-                    if (lane >= o) PS::add(v, t);
+                    const T t = __shfl_up_sync(0xffffffffu, v[p], o);
+                    if (lane >= o) v[p] += t;
                 }
-                E tot = carry[p];
-                PS::add(tot, v);
-                if (j < NL) Ps[p * (NL + 1) + j + 1] = tot;
-                PS::add(carry[p], PS::shfl(v, 31));
+                if (j < NL) Ps[p * (NL + 1) + j + 1] = carry[p] + v[p];
+                carry[p] += __shfl_sync(0xffffffffu, v[p], 31);
             }
         }
     }
@@ -651,8 +619,8 @@ __device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const i
     const T *aL = dc.axis[L];
     int nouter = dc.cart_n[0];
     if (D == 3) nouter *= dc.cart_n[1];
-    CSum<T> acc[M];
-    for (int o = lane; o < nouter; o += 32) {
+    // the terms of outer node o (both sides), added into acc[0..M)
+    auto terms = [&](int o, T *acc) {
         int idx[2] = {o % dc.cart_n[0], D == 3 ? o / dc.cart_n[0] : 0};
         T uo[2];
         uo[0] = dc.axis[0][idx[0]];
@@ -683,14 +651,14 @@ __device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const i
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const T *r = side[s];
-            const E *Ps = P + s * 3 * (NL + 1);
+            const T *Ps = P + s * 3 * (NL + 1);
             const bool lo_side = (s == 0) != asc;        // the full range starts at 0
             const int f0 = lo_side ? 0 : jb, f1 = lo_side ? ja : NL;
             T Y[3];
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
-                const E *Pp = Ps + p * (NL + 1);
-                Y[p] = (T)PS::range(Pp[f1], Pp[f0], Pp[jb], Pp[ja]);
+                const T *Pp = Ps + p * (NL + 1);
+                Y[p] = (Pp[f1] - Pp[f0]) + T(0.5) * (Pp[jb] - Pp[ja]);
             }
             T go = r[GR_PREF];
 #pragma unroll
@@ -699,17 +667,40 @@ __device__ __forceinline__ void face_sum1_sep_body(const DevCase<T> &dc, const i
                 go *= dc.axw[e][idx[e]] * gauss<T>(r[GR_LAM], r[GR_NL2], dv * dv);
             }
             const T g = go;
-            acc[0].add(g * Y[0]);
+            acc[0] += g * Y[0];
 #pragma unroll
-            for (int e = 0; e < D - 1; ++e) acc[1 + e].add(g * co[e] * Y[0]);
-            acc[1 + L].add(g * Y[1]);
-            acc[D + 1].add(T(0.5) * g * (co2 * Y[0] + Y[2] + r[GR_NB] * Y[0]));
+            for (int e = 0; e < D - 1; ++e) acc[1 + e] += g * co[e] * Y[0];
+            acc[1 + L] += g * Y[1];
+            acc[D + 1] += T(0.5) * g * (co2 * Y[0] + Y[2] + r[GR_NB] * Y[0]);
         }
-    }
+    };
+    if constexpr (std::is_same<T, float>::value) {
+        // blocked sums accumulated in FP64 (SUM_BLOCK outer nodes per lane per block)
+        constexpr int NP = M <= 4 ? 4 : 8;
+        double acc = 0.0;
+        for (int o0 = 0; o0 < nouter; o0 += 32 * SUM_BLOCK) {
+            float blk[NP];
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-        const double sm = warp_sum(acc[m].value());
-        if (lane == 0) dc.fsum1[(size_t)f * M + m] = sm;
+            for (int i = 0; i < NP; ++i) blk[i] = 0.f;
+            for (int j = 0; j < SUM_BLOCK; ++j) {
+                const int o = o0 + 32 * j + lane;
+                if (o >= nouter) break;
+                terms(o, blk);
+            }
+            acc += block_to_fp64<NP>(blk);
+        }
+        const int vi = lane >> (NP == 4 ? 3 : 2);
+        if ((lane & (NP == 4 ? 7 : 3)) == 0 && vi < M) dc.fsum1[(size_t)f * M + vi] = acc;
+    } else {
+        T acc[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc[m] = 0;
+        for (int o = lane; o < nouter; o += 32) terms(o, acc);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const double sm = warp_sum(acc[m]);
+            if (lane == 0) dc.fsum1[(size_t)f * M + m] = sm;
+        }
     }
 }
 
@@ -897,51 +888,63 @@ __device__ __forceinline__ void face_sum2_body(const DevCase<T> &dc, const int b
     for (int d = 0; d < D; ++d) U0[d] = fr[FR_U + d];
     const T lam = fr[FR_LAM], pref = fr[FR_PREF], nl2 = fr[FR_NL2];
     using Mo = Mono<D>;
-    // FP32 form: blocks of SUM_BLOCK terms summed directly, block sums
-    // compensated, lanes combined in FP64 (as in k_face_sum1)
-    constexpr int B = std::is_same<T, float>::value ? SUM_BLOCK : 1;
-    CSum<T> r[Mo::N];
-    for (int k0 = lane; k0 < dc.nvp; k0 += 32 * B) {
-        T blk[Mo::N];
+    // the distinct monomial moments of velocity k, added into r[0..Mo::N)
+    auto terms = [&](int k, T *r) {
+        T uk[3], wk, c[D], c2 = 0;
+        load_uw(dc.uw, k, uk, wk);
 #pragma unroll
-        for (int i = 0; i < Mo::N; ++i) blk[i] = 0;
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            const int k = k0 + 32 * j;
-            if (B > 1 && k >= dc.nvp) break;
-            T c[D], c2 = 0;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                c[d] = dc.u[d][k] - U0[d];
-                c2 += c[d] * c[d];
-            }
-            const T a = dc.w[k] * pref * gauss<T>(lam, nl2, c2);
-            blk[0] += a;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const T a1 = a * c[d];
-                blk[Mo::O1 + d] += a1;
-#pragma unroll
-                for (int e = d; e < D; ++e) {
-                    const T a2 = a1 * c[e];
-                    blk[Mo::O2 + pair_index(D, d, e)] += a2;
-                    blk[Mo::OQ2 + pair_index(D, d, e)] += a2 * c2;
-#pragma unroll
-                    for (int g = e; g < D; ++g) blk[Mo::O3 + triple_index(D, d, e, g)] += a2 * c[g];
-                }
-            }
-            const T a4 = a * c2 * c2;
-            blk[Mo::OQ4] += a4;
-#pragma unroll
-            for (int d = 0; d < D; ++d) blk[Mo::OQ4 + 1 + d] += a4 * c[d];
+        for (int d = 0; d < D; ++d) {
+            c[d] = uk[d] - U0[d];
+            c2 += c[d] * c[d];
         }
+        const T a = wk * pref * gauss<T>(lam, nl2, c2);
+        r[0] += a;
 #pragma unroll
-        for (int i = 0; i < Mo::N; ++i) r[i].add(blk[i]);
-    }
+        for (int d = 0; d < D; ++d) {
+            const T a1 = a * c[d];
+            r[Mo::O1 + d] += a1;
 #pragma unroll
-    for (int i = 0; i < Mo::N; ++i) {
-        const double sm = warp_sum(r[i].value());
-        if (lane == 0) dc.fsum2[(size_t)f * S2 + i] = sm;
+            for (int e = d; e < D; ++e) {
+                const T a2 = a1 * c[e];
+                r[Mo::O2 + pair_index(D, d, e)] += a2;
+                r[Mo::OQ2 + pair_index(D, d, e)] += a2 * c2;
+#pragma unroll
+                for (int g = e; g < D; ++g) r[Mo::O3 + triple_index(D, d, e, g)] += a2 * c[g];
+            }
+        }
+        const T a4 = a * c2 * c2;
+        r[Mo::OQ4] += a4;
+#pragma unroll
+        for (int d = 0; d < D; ++d) r[Mo::OQ4 + 1 + d] += a4 * c[d];
+    };
+    if constexpr (std::is_same<T, float>::value) {
+        // blocked sums accumulated in FP64 (SUM_BLOCK terms per lane per block)
+        constexpr int NP = Mo::N <= 16 ? 16 : 32;
+        double acc = 0.0;
+        for (int k0 = lane; k0 < dc.nvp; k0 += 32 * SUM_BLOCK) {
+            float blk[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) blk[i] = 0.f;
+#pragma unroll 2
+            for (int j = 0; j < SUM_BLOCK; ++j) {
+                const int k = k0 + 32 * j;
+                if (k >= dc.nvp) break;              // uniform: nvp is a multiple of 32
+                terms(k, blk);
+            }
+            acc += block_to_fp64<NP>(blk);
+        }
+        const int vi = lane >> (NP == 16 ? 1 : 0);
+        if ((lane & (NP == 16 ? 1 : 0)) == 0 && vi < Mo::N) dc.fsum2[(size_t)f * S2 + vi] = acc;
+    } else {
+        T r[Mo::N];
+#pragma unroll
+        for (int i = 0; i < Mo::N; ++i) r[i] = 0;
+        for (int k = lane; k < dc.nvp; k += 32) terms(k, r);
+#pragma unroll
+        for (int i = 0; i < Mo::N; ++i) {
+            const double sm = warp_sum(r[i]);
+            if (lane == 0) dc.fsum2[(size_t)f * S2 + i] = sm;
+        }
     }
 }
 
@@ -977,20 +980,41 @@ __device__ __forceinline__ void face_sum2_sep_body(const DevCase<T> &dc, const i
     double *out = dc.fsum2 + (size_t)f * NS * (D + 1);
     for (int d = 0; d < D; ++d) {
         const T U0 = fr[FR_U + d];
-        CSum<T> acc[6];
-        for (int i = lane; i < dc.cart_n[d]; i += 32) {
-            const T c = dc.axis[d][i] - U0;
-            T v = dc.axw[d][i] * gauss<T>(lam, nl2, c * c);
+        if constexpr (std::is_same<T, float>::value) {
+            // blocked sums accumulated in FP64 (SUM_BLOCK nodes per lane per block)
+            double acc = 0.0;
+            for (int i0 = 0; i0 < dc.cart_n[d]; i0 += 32 * SUM_BLOCK) {
+                float blk[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int j = 0; j < SUM_BLOCK; ++j) {
+                    const int i = i0 + 32 * j + lane;
+                    if (i >= dc.cart_n[d]) break;
+                    const float c = dc.axis[d][i] - U0;
+                    float v = dc.axw[d][i] * gauss<float>(lam, nl2, c * c);
+#pragma unroll
+                    for (int pw = 0; pw < 6; ++pw) {
+                        blk[pw] += v;
+                        v *= c;
+                    }
+                }
+                acc += block_to_fp64<8>(blk);
+            }
+            if ((lane & 3) == 0 && (lane >> 2) < 6) out[d * 6 + (lane >> 2)] = acc;
+        } else {
+            T acc[6] = {0, 0, 0, 0, 0, 0};
+            for (int i = lane; i < dc.cart_n[d]; i += 32) {
+                const T c = dc.axis[d][i] - U0;
+                T v = dc.axw[d][i] * gauss<T>(lam, nl2, c * c);
+#pragma unroll
+                for (int pw = 0; pw < 6; ++pw) {
+                    acc[pw] += v;
+                    v *= c;
+                }
+            }
 #pragma unroll
             for (int pw = 0; pw < 6; ++pw) {
-                acc[pw].add(v);
-                v *= c;
+                const double sm = warp_sum(acc[pw]);
+                if (lane == pw) out[d * 6 + pw] = sm;
             }
-        }
-#pragma unroll
-        for (int pw = 0; pw < 6; ++pw) {
-            const double sm = warp_sum(acc[pw].value());
-            if (lane == pw) out[d * 6 + pw] = sm;
         }
     }
 }
@@ -1366,8 +1390,10 @@ __global__ void __launch_bounds__(256) k_wall_sum_batch(const DevCase<T> *__rest
 }
 
 // ------------------------------------------------------------ gather pass
-// One CTA per (patch of P consecutive cells, tile of V = 32*TV velocities);
-// lane l handles the TV consecutive velocities V*tile + TV*l + j.
+// One CTA per (patch of P consecutive cells, group of G = vt_group consecutive
+// velocity tiles of V = 32*TV velocities); the CTA takes the group's tiles one
+// after the other, and in a tile lane l handles the TV consecutive velocities
+// V*tile + TV*l + j.  Per tile:
 // Phase A: limited slopes of the patch cells and their face neighbours (ring)
 //          into shared memory, each computed once.
 // Phase B: per patch cell, the flux of every face (Eq. microscopicFlux with
@@ -1377,212 +1403,276 @@ __global__ void __launch_bounds__(256) k_wall_sum_batch(const DevCase<T> *__rest
 //          macroscopicUpdata / macroscopicFlux).  The cell's own f and slopes
 //          stay in registers; every face entry is read once for all TV
 //          velocities of the lane.
+// The moments of a cell accumulate over the group's tiles in shared memory
+// (the warp that owns a cell is the same for every tile) and are written once
+// per (cell, group).  Consecutive tiles of a patch re-read its face entries
+// and records from the SM's cache.
+//
+// Shared memory: the moment accumulators, P x 16 values of T (FP32: the
+// double-float pair of each of up to 8 moments; FP64: the moments), then the
+// slope buffer, (patch + ring) x NC x D x V values of T.
+template <typename T>
+__host__ __device__ constexpr int gather_acc_values(int P) { return P * 16; }
+
 template <typename T, int D, int NC, int TV>
-__device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, const int vt, T *sg)
+__device__ __forceinline__ void gather_item(const DevCase<T> &dc, const int p, const int grp, T *sg)
 {
     constexpr int V = 32 * TV;
     constexpr int M = D + 2;
+    // velocities per lane of the slope pass: twice TV in the FP32 form with one
+    // stored component (a half-warp per slope cell), else TV (registers)
+    constexpr int TVA = std::is_same<T, float>::value && NC == 1 && TV <= 2 ? 2 * TV : TV;
     using E = GEnt<D>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int kl = vt * V + TV * lane;
     const int cb = p * dc.P;
     const int npc = min(dc.P, dc.C - cb);
     const int rb = dc.ring_ptr[p], re = dc.ring_ptr[p + 1];
     const int nslope = npc + (re - rb);
     const int nvp = dc.nvp;
     const size_t rs = (size_t)NC * nvp;
-    const T *__restrict__ fl = dc.f_cur + kl;
-    T *const sl = sg + TV * lane;               // this lane's column of the slope buffer
+    T *const sacc = sg;                         // moment accumulators [P][16]
+    T *const sl = sg + gather_acc_values<T>(dc.P) + TV * lane;   // this lane's column of the slope buffer
+    for (int i = threadIdx.x; i < gather_acc_values<T>(dc.P); i += blockDim.x) sacc[i] = T(0);
+    const int vt0 = grp * dc.vt_group, vt1 = min(dc.n_vt, vt0 + dc.vt_group);
+    for (int vt = vt0; vt < vt1; ++vt) {
+        const int kl = vt * V + TV * lane;
+        const T *__restrict__ fl = dc.f_cur + kl;
 
-    T u[3][TV];
-    ldv<T, TV>(dc.u[0] + kl, u[0]);
-    ldv<T, TV>(dc.u[1] + kl, u[1]);
-    if (D == 3) ldv<T, TV>(dc.u[2] + kl, u[2]);
-    else
+        T u[3][TV];
+        auto load_u = [&](int k, auto &uu) {
+            constexpr int N = sizeof(uu[0]) / sizeof(T);
+            ldv<T, N>(dc.u[0] + k, uu[0]);
+            ldv<T, N>(dc.u[1] + k, uu[1]);
+            if (D == 3) ldv<T, N>(dc.u[2] + k, uu[2]);
+            else
 #pragma unroll
-        for (int j = 0; j < TV; ++j) u[2][j] = T(0);
+                for (int j = 0; j < N; ++j) uu[2][j] = T(0);
+        };
 
-    // ---- phase A: slopes (micro reconstruction of the velocity loop, Algorithm 1)
-    for (int s = warp; s < nslope; s += nwarps) {
-        const int c = s < npc ? cb + s : dc.ring_cells[rb + s - npc];
-        T g[NC][D][TV], fi[NC][TV];
-        cell_slope_tv<T, D, NC, TV>(dc, fl, c, u, g, fi);
+        // ---- phase A: slopes (micro reconstruction of the velocity loop, Algorithm 1)
+        if constexpr (TVA == TV) {
+            load_u(kl, u);
+            for (int s = warp; s < nslope; s += nwarps) {
+                const int c = s < npc ? cb + s : dc.ring_cells[rb + s - npc];
+                T g[NC][D][TV], fi[NC][TV];
+                cell_slope_tv<T, D, NC, TV>(dc, fl, c, u, g, fi);
 #pragma unroll
-        for (int m = 0; m < NC; ++m)
+                for (int m = 0; m < NC; ++m)
 #pragma unroll
-            for (int d = 0; d < D; ++d) stv<T, TV>(sl + ((s * NC + m) * D + d) * V, g[m][d]);
-    }
-    __syncthreads();
-
-    // ---- phase B: fluxes, stage 1, moments (velocity loop and wall flux, Algorithm 1)
-    const T dt = dc.dtT;
-    const T hdt2 = T(0.5) * dc.dtT * dc.dtT;
-    for (int s = warp; s < npc; s += nwarps) {
-        const int c = cb + s;
-        T fs[NC][TV], gs[NC][D][TV], R[NC][TV];
+                    for (int d = 0; d < D; ++d) stv<T, TV>(sl + ((s * NC + m) * D + d) * V, g[m][d]);
+            }
+        } else {
+            // each half-warp takes a slope cell, TVA velocities per lane: the
+            // face entries are read once for twice the velocities
+            const int hl = lane & 15;
+            const int klA = vt * V + TVA * hl;
+            T ua[3][TVA];
+            load_u(klA, ua);
+            const T *__restrict__ fla = dc.f_cur + klA;
+            T *const sla = sg + gather_acc_values<T>(dc.P) + TVA * hl;
+            for (int s = 2 * warp + (lane >> 4); s < nslope; s += 2 * nwarps) {
+                const int c = s < npc ? cb + s : dc.ring_cells[rb + s - npc];
+                T g[NC][D][TVA], fi[NC][TVA];
+                cell_slope_tv<T, D, NC, TVA>(dc, fla, c, ua, g, fi);
 #pragma unroll
-        for (int m = 0; m < NC; ++m) {
-            ldv<T, TV>(fl + (size_t)c * rs + (size_t)m * nvp, fs[m]);
+                for (int m = 0; m < NC; ++m)
 #pragma unroll
-            for (int d = 0; d < D; ++d) ldv_s<T, TV>(sl + ((s * NC + m) * D + d) * V, gs[m][d]);
-#pragma unroll
-            for (int j = 0; j < TV; ++j) R[m][j] = 0;
+                    for (int d = 0; d < D; ++d) stv<T, TVA>(sla + ((s * NC + m) * D + d) * V, g[m][d]);
+            }
+            load_u(kl, u);
         }
-        const int e0 = __ldg(dc.cf_ptr + c), e1 = __ldg(dc.cf_ptr + c + 1);
+        __syncthreads();
+
+        // ---- phase B: fluxes, stage 1, moments (velocity loop and wall flux, Algorithm 1)
+        const T dt = dc.dtT;
+        const T hdt2 = T(0.5) * dc.dtT * dc.dtT;
+        for (int s = warp; s < npc; s += nwarps) {
+            const int c = cb + s;
+            T fs[NC][TV], gs[NC][D][TV], R[NC][TV];
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                ldv<T, TV>(fl + (size_t)c * rs + (size_t)m * nvp, fs[m]);
+#pragma unroll
+                for (int d = 0; d < D; ++d) ldv_s<T, TV>(sl + ((s * NC + m) * D + d) * V, gs[m][d]);
+#pragma unroll
+                for (int j = 0; j < TV; ++j) R[m][j] = 0;
+            }
+            const int e0 = __ldg(dc.cf_ptr + c), e1 = __ldg(dc.cf_ptr + c + 1);
 #pragma unroll 4
-        for (int e = e0; e < e1; ++e) {
-            const int4 gi = __ldg(dc.gi + e);
-            T ge[E::LEN];
-            load_rec<E::LEN>(dc.gf + (size_t)e * E::LEN, ge);
-            const T cs = ge[E::CS];
-            T un[TV];
-#pragma unroll
-            for (int j = 0; j < TV; ++j) {
-                const T uj[3] = {u[0][j], u[1][j], u[2][j]};
-                un[j] = normal_velocity<T, D>(uj, ge + E::N);
-            }
-            if (gi.z == FT_WALL) {
-                T wr[GREC];
-                load_rec<GREC>(dc.wrec + (size_t)gi.x * GREC, wr);
-#pragma unroll
-                for (int j = 0; j < TV; ++j) {
-                    const T uj[3] = {u[0][j], u[1][j], u[2][j]};
-                    T F[NC];
-                    if (un[j] > T(0)) {
-#pragma unroll
-                        for (int m = 0; m < NC; ++m) {
-                            T fin = fs[m][j], ug = 0;
-#pragma unroll
-                            for (int d = 0; d < D; ++d) {
-                                fin += gs[m][d][j] * ge[E::RS + d];
-                                ug += uj[d] * gs[m][d][j];
-                            }
-                            F[m] = un[j] * (dt * fin - hdt2 * ug);
-                        }
-                    } else {
-                        const T H = maxwell_h<T, D>(wr, uj);
-                        F[0] = un[j] * dt * H;
-                        if (NC == 2) F[NC - 1] = un[j] * dt * wr[GR_NB] * H;
-                    }
-#pragma unroll
-                    for (int m = 0; m < NC; ++m) R[m][j] += cs * F[m];
+            for (int e = e0; e < e1; ++e) {
+                const int4 gi = __ldg(dc.gi + e);
+                T ge[E::LEN];
+                if constexpr (E::SKIP1 > E::SKIP0) {
+                    load_rec<E::SKIP0>(dc.gf + (size_t)e * E::LEN, *reinterpret_cast<T (*)[E::SKIP0]>(ge));
+                    load_rec<E::LEN - E::SKIP1>(dc.gf + (size_t)e * E::LEN + E::SKIP1,
+                                                *reinterpret_cast<T (*)[E::LEN - E::SKIP1]>(ge + E::SKIP1));
+                } else {
+                    load_rec<E::LEN>(dc.gf + (size_t)e * E::LEN, ge);
                 }
-                continue;
-            }
-            T fr[XREC];
-            load_rec<XREC>(dc.xrec + (size_t)gi.y * XREC, fr);
-            if (gi.z == FT_FARFIELD) {
-                T gr[GREC];
-                load_rec<GREC>(dc.grec + (size_t)gi.x * GREC, gr);
+                const T cs = ge[E::CS];
+                T un[TV];
 #pragma unroll
                 for (int j = 0; j < TV; ++j) {
                     const T uj[3] = {u[0][j], u[1][j], u[2][j]};
-                    T fup[NC], ugf[NC], F[NC];
-                    if (un[j] > T(0)) {
+                    un[j] = normal_velocity<T, D>(uj, ge + E::N);
+                }
+                if (gi.z == FT_WALL) {
+                    T wr[GREC];
+                    load_rec<GREC>(dc.wrec + (size_t)gi.x * GREC, wr);
 #pragma unroll
-                        for (int m = 0; m < NC; ++m) {
-                            T v = fs[m][j], ug = 0;
+                    for (int j = 0; j < TV; ++j) {
+                        const T uj[3] = {u[0][j], u[1][j], u[2][j]};
+                        T F[NC];
+                        if (un[j] > T(0)) {
 #pragma unroll
-                            for (int d = 0; d < D; ++d) {
-                                v += gs[m][d][j] * ge[E::RS + d];
-                                ug += uj[d] * gs[m][d][j];
+                            for (int m = 0; m < NC; ++m) {
+                                T fin = fs[m][j], ug = 0;
+#pragma unroll
+                                for (int d = 0; d < D; ++d) {
+                                    fin += gs[m][d][j] * ge[E::RS + d];
+                                    ug += uj[d] * gs[m][d][j];
+                                }
+                                F[m] = un[j] * (dt * fin - hdt2 * ug);
                             }
-                            fup[m] = v;
-                            ugf[m] = ug;
+                        } else {
+                            const T H = maxwell_h<T, D>(wr, uj);
+                            F[0] = un[j] * dt * H;
+                            if (NC == 2) F[NC - 1] = un[j] * dt * wr[GR_NB] * H;
                         }
-                    } else {
-                        const T H = maxwell_h<T, D>(gr, uj);
-                        fup[0] = H;
-                        if (NC == 2) fup[NC - 1] = gr[GR_NB] * H;
 #pragma unroll
-                        for (int m = 0; m < NC; ++m) ugf[m] = 0;
+                        for (int m = 0; m < NC; ++m) R[m][j] += cs * F[m];
+                    }
+                    continue;
+                }
+                T fr[XREC];
+                load_rec<XREC>(dc.xrec + (size_t)gi.y * XREC, fr);
+                if (gi.z == FT_FARFIELD) {
+                    T gr[GREC];
+                    load_rec<GREC>(dc.grec + (size_t)gi.x * GREC, gr);
+#pragma unroll
+                    for (int j = 0; j < TV; ++j) {
+                        const T uj[3] = {u[0][j], u[1][j], u[2][j]};
+                        T fup[NC], ugf[NC], F[NC];
+                        if (un[j] > T(0)) {
+#pragma unroll
+                            for (int m = 0; m < NC; ++m) {
+                                T v = fs[m][j], ug = 0;
+#pragma unroll
+                                for (int d = 0; d < D; ++d) {
+                                    v += gs[m][d][j] * ge[E::RS + d];
+                                    ug += uj[d] * gs[m][d][j];
+                                }
+                                fup[m] = v;
+                                ugf[m] = ug;
+                            }
+                        } else {
+                            const T H = maxwell_h<T, D>(gr, uj);
+                            fup[0] = H;
+                            if (NC == 2) fup[NC - 1] = gr[GR_NB] * H;
+#pragma unroll
+                            for (int m = 0; m < NC; ++m) ugf[m] = 0;
+                        }
+                        interface_flux<T, D, NC>(fr, uj, un[j], fup, ugf, F);
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) R[m][j] += cs * F[m];
+                    }
+                    continue;
+                }
+                // interior or periodic: the neighbour's f and slopes
+                T fo[NC][TV], go[NC][D][TV];
+                const T *so = sl + (size_t)gi.w * NC * D * V;
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    ldv<T, TV>(fl + (size_t)gi.x * rs + (size_t)m * nvp, fo[m]);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) ldv_s<T, TV>(so + (m * D + d) * V, go[m][d]);
+                }
+#pragma unroll
+                for (int j = 0; j < TV; ++j) {
+                    const T uj[3] = {u[0][j], u[1][j], u[2][j]};
+                    const bool self = un[j] > T(0);
+                    T fup[NC], ugf[NC], F[NC];
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) {
+                        T v = self ? fs[m][j] : fo[m][j], ug = 0;
+#pragma unroll
+                        for (int d = 0; d < D; ++d) {
+                            const T gd = self ? gs[m][d][j] : go[m][d][j];
+                            v += gd * (self ? ge[E::RS + d] : ge[E::RO + d]);
+                            ug += uj[d] * gd;
+                        }
+                        fup[m] = v;
+                        ugf[m] = ug;
                     }
                     interface_flux<T, D, NC>(fr, uj, un[j], fup, ugf, F);
 #pragma unroll
                     for (int m = 0; m < NC; ++m) R[m][j] += cs * F[m];
                 }
-                continue;
             }
-            // interior or periodic: the neighbour's f and slopes
-            T fo[NC][TV], go[NC][D][TV];
-            const T *so = sl + (size_t)gi.w * NC * D * V;
+            // stage 1 and the moments of R
+            T cr[CREC];
+            load_rec<CREC>(dc.crec + (size_t)c * CREC, cr);
+            const T cc = cr[CR_C];
+            T wk[TV];
+            ldv<T, TV>(dc.w + kl, wk);
+            // moments sum_k w psi_k R_k of this tile: FP64 sums in the FP64 form;
+            // in the FP32 form each term is an FP32 product, and the sums over the
+            // lane's velocities and across the warp are double-float (error-free
+            // additions), widened to FP64 for the W update
+            constexpr int NR = M <= 4 ? 4 : 8;
+            T mh[NR], ml[NR];
 #pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                ldv<T, TV>(fl + (size_t)gi.x * rs + (size_t)m * nvp, fo[m]);
-#pragma unroll
-                for (int d = 0; d < D; ++d) ldv_s<T, TV>(so + (m * D + d) * V, go[m][d]);
-            }
+            for (int i = 0; i < NR; ++i) mh[i] = ml[i] = T(0);
+            T out[NC][TV];
 #pragma unroll
             for (int j = 0; j < TV; ++j) {
                 const T uj[3] = {u[0][j], u[1][j], u[2][j]};
-                const bool self = un[j] > T(0);
-                T fup[NC], ugf[NC], F[NC];
+                T fp[NC];
+                shakhov_fplus<T, D, NC>(cr, uj, fp);
 #pragma unroll
-                for (int m = 0; m < NC; ++m) {
-                    T v = self ? fs[m][j] : fo[m][j], ug = 0;
+                for (int m = 0; m < NC; ++m) out[m][j] = fs[m][j] + R[m][j] + cc * (fp[m] - fs[m][j]);
+                T u2 = 0;
 #pragma unroll
-                    for (int d = 0; d < D; ++d) {
-                        const T gd = self ? gs[m][d][j] : go[m][d][j];
-                        v += gd * (self ? ge[E::RS + d] : ge[E::RO + d]);
-                        ug += uj[d] * gd;
+                for (int d = 0; d < D; ++d) u2 += uj[d] * uj[d];
+                const T wr0 = wk[j] * R[0][j];
+                T x[M];
+                x[0] = wr0;
+#pragma unroll
+                for (int d = 0; d < D; ++d) x[1 + d] = uj[d] * wr0;
+                x[D + 1] = T(0.5) * (u2 * wr0 + (NC == 2 ? wk[j] * R[NC - 1][j] : T(0)));
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    if constexpr (std::is_same<T, float>::value) {
+                        if (j == 0) mh[i] = x[i];
+                        else ff_add(mh[i], ml[i], x[i], 0.f);
+                    } else {
+                        mh[i] += x[i];
                     }
-                    fup[m] = v;
-                    ugf[m] = ug;
-                }
-                interface_flux<T, D, NC>(fr, uj, un[j], fup, ugf, F);
-#pragma unroll
-                for (int m = 0; m < NC; ++m) R[m][j] += cs * F[m];
-            }
-        }
-        // stage 1 and the moments of R
-        T cr[CREC];
-        load_rec<CREC>(dc.crec + (size_t)c * CREC, cr);
-        const T cc = cr[CR_C];
-        T wk[TV];
-        ldv<T, TV>(dc.w + kl, wk);
-        // moments sum_k w psi_k R_k of this tile: FP64 sums in the FP64 form;
-        // in the FP32 form each term is an FP32 product, and the sums over the
-        // lane's velocities and across the warp are double-float (error-free
-        // additions), widened to FP64 for the W update
-        constexpr int NR = M <= 4 ? 4 : 8;
-        T mh[NR], ml[NR];
-#pragma unroll
-        for (int i = 0; i < NR; ++i) mh[i] = ml[i] = T(0);
-        T out[NC][TV];
-#pragma unroll
-        for (int j = 0; j < TV; ++j) {
-            const T uj[3] = {u[0][j], u[1][j], u[2][j]};
-            T fp[NC];
-            shakhov_fplus<T, D, NC>(cr, uj, fp);
-#pragma unroll
-            for (int m = 0; m < NC; ++m) out[m][j] = fs[m][j] + R[m][j] + cc * (fp[m] - fs[m][j]);
-            T u2 = 0;
-#pragma unroll
-            for (int d = 0; d < D; ++d) u2 += uj[d] * uj[d];
-            const T wr0 = wk[j] * R[0][j];
-            T x[M];
-            x[0] = wr0;
-#pragma unroll
-            for (int d = 0; d < D; ++d) x[1 + d] = uj[d] * wr0;
-            x[D + 1] = T(0.5) * (u2 * wr0 + (NC == 2 ? wk[j] * R[NC - 1][j] : T(0)));
-#pragma unroll
-            for (int i = 0; i < M; ++i) {
-                if constexpr (std::is_same<T, float>::value) {
-                    if (j == 0) mh[i] = x[i];
-                    else ff_add(mh[i], ml[i], x[i], 0.f);
-                } else {
-                    mh[i] += x[i];
                 }
             }
-        }
 #pragma unroll
-        for (int m = 0; m < NC; ++m) stv<T, TV>(dc.f_nxt + kl + (size_t)c * rs + (size_t)m * nvp, out[m]);
-        double sm;
-        if constexpr (std::is_same<T, float>::value) sm = warp_transpose_sum_ff<NR>(mh, ml);
-        else sm = warp_transpose_sum<T, NR>(mh);
-        const int vi = lane >> (NR == 4 ? 3 : 2);
-        if ((lane & (NR == 4 ? 7 : 3)) == 0 && vi < M)
-            dc.dW_part[((size_t)c * dc.n_vt + vt) * M + vi] = sm;
+            for (int m = 0; m < NC; ++m) stv<T, TV>(dc.f_nxt + kl + (size_t)c * rs + (size_t)m * nvp, out[m]);
+            const int vi = lane >> (NR == 4 ? 3 : 2);
+            const bool holder = (lane & (NR == 4 ? 7 : 3)) == 0 && vi < M;
+            if constexpr (std::is_same<T, float>::value) {
+                float oh, ol;
+                warp_transpose_sum_ff2<NR>(mh, ml, oh, ol);
+                if (holder) ff_add(sacc[s * 16 + vi], sacc[s * 16 + 8 + vi], oh, ol);
+            } else {
+                const T sm = warp_transpose_sum<T, NR>(mh);
+                if (holder) sacc[s * 16 + vi] += sm;
+            }
+        }
+        __syncthreads();                        // the next tile's slopes overwrite the buffer
+    }
+    // the moments of the group, once per (cell, group), by the warp that owns the cell
+    for (int s = warp; s < npc; s += nwarps) {
+        const int vi = lane >> (M <= 4 ? 3 : 2);
+        if ((lane & (M <= 4 ? 7 : 3)) == 0 && vi < M) {
+            double v = (double)sacc[s * 16 + vi];
+            if constexpr (std::is_same<T, float>::value) v += (double)sacc[s * 16 + 8 + vi];
+            dc.dW_part[((size_t)(cb + s) * dc.n_groups + grp) * M + vi] = v;
+        }
     }
 }
 
@@ -1595,20 +1685,15 @@ template <typename T, int D, int NC, int TV, int NTH>
 __global__ void __launch_bounds__(NTH, NTH >= 512 ? 2 : 0) k_gather(DevCase<T> dc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // One-dimensional grid of n_patches x n_vt blocks in groups of G = vt_group
-    // consecutive velocity tiles: within a group the patches follow each other
-    // and the G tiles of a patch are adjacent, so a patch's face entries and
-    // records are fetched from DRAM once per group, not once per tile, when a
-    // sweep over all patches does not fit L2 (large 3D meshes).  G = 1 is the
-    // plain patch-major sweep of one tile after another.
-    const int G = dc.vt_group, per = dc.n_patches * G;
-    const int grp = blockIdx.x / per, base = grp * G, gsz = min(G, dc.n_vt - base);
-    const int r = blockIdx.x - grp * per;
-    gather_item<T, D, NC, TV>(dc, r / gsz, base + r % gsz, reinterpret_cast<T *>(smem_raw));
+    // One-dimensional grid of n_patches x n_groups blocks, patches fastest:
+    // the CTAs in flight cover neighbouring patches in the same tile group,
+    // so the rows of f they share (ring cells) are read from L2.
+    const int grp = blockIdx.x / dc.n_patches;
+    gather_item<T, D, NC, TV>(dc, blockIdx.x - grp * dc.n_patches, grp, reinterpret_cast<T *>(smem_raw));
 }
 
 // Persistent gather over many cases: a fixed grid of CTAs walks a work list of
-// (case, patch, velocity tile) items; each item is exactly the CTA of k_gather
+// (case, patch, tile group) items; each item is exactly the CTA of k_gather
 // for that case, so every case gets bit-identical results alone or batched.
 template <typename T, int D, int NC, int TV, int NTH>
 __global__ void __launch_bounds__(NTH, NTH >= 512 ? 2 : 0) k_gather_batch(const DevCase<T> *__restrict__ cases,
@@ -1636,7 +1721,7 @@ __device__ __forceinline__ void update_W_body(const DevCase<T> &dc, const int bx
         const bool counts = !dc.owned || dc.owned[c];      // halo cells of a subdomain do not count
         for (int m = 0; m < M; ++m) {
             double s = 0.0;
-            for (int t = 0; t < dc.n_vt; ++t) s += dc.dW_part[((size_t)c * dc.n_vt + t) * M + m];
+            for (int t = 0; t < dc.n_groups; ++t) s += dc.dW_part[((size_t)c * dc.n_groups + t) * M + m];
             if (counts) {
                 wsq[m] = Wc[m] * Wc[m];
                 dsq[m] = s * s;
@@ -1730,48 +1815,74 @@ __device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx)
     T U[D];
     for (int d = 0; d < D; ++d) U[d] = kr[CR_U + d];
     const size_t rs = (size_t)NC * dc.nvp;
-    CSum<T> acc[D];
-    for (int k0 = 4 * lane; k0 < dc.nvp; k0 += 128) {
-        T ft[NC][4], fn[NC][4];
+    // heat-flux terms: FP64 sums in the FP64 form; blocked sums accumulated in
+    // FP64 in the FP32 form (16 terms per lane per block)
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int NP = D == 2 ? 2 : 4;
+    T blk[NP];
 #pragma unroll
-        for (int m = 0; m < NC; ++m) {
-            const V4 v = *reinterpret_cast<const V4 *>(dc.f_nxt + (size_t)c * rs + (size_t)m * dc.nvp + k0);
-            ft[m][0] = v.x;
-            ft[m][1] = v.y;
-            ft[m][2] = v.z;
-            ft[m][3] = v.w;
-        }
+    for (int d = 0; d < NP; ++d) blk[d] = 0;
+    double acc = 0.0;
+    int nblk = 0;
+    for (int k00 = 0; k00 < dc.nvp; k00 += 128) {          // uniform over the warp
+        const int k0 = k00 + 4 * lane;
+        if (k0 < dc.nvp) {
+            T ft[NC][4], fn[NC][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int k = k0 + j;
-            T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
-            T fp[NC];
-            shakhov_fplus<T, D, NC>(kr, u, fp);
-#pragma unroll
-            for (int m = 0; m < NC; ++m) fn[m][j] = (ft[m][j] + cc * fp[m]) * inv;
-            T cv[D], c2 = 0;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                cv[d] = u[d] - U[d];
-                c2 += cv[d] * cv[d];
+            for (int m = 0; m < NC; ++m) {
+                const V4 v = *reinterpret_cast<const V4 *>(dc.f_nxt + (size_t)c * rs + (size_t)m * dc.nvp + k0);
+                ft[m][0] = v.x;
+                ft[m][1] = v.y;
+                ft[m][2] = v.z;
+                ft[m][3] = v.w;
             }
-            const T we = dc.w[k] * (c2 * fn[0][j] + (NC == 2 ? fn[NC - 1][j] : T(0)));
 #pragma unroll
-            for (int d = 0; d < D; ++d) acc[d].add(cv[d] * we);
+            for (int j = 0; j < 4; ++j) {
+                const int k = k0 + j;
+                T u[3], wk;
+                load_uw(dc.uw, k, u, wk);
+                T fp[NC];
+                shakhov_fplus<T, D, NC>(kr, u, fp);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) fn[m][j] = (ft[m][j] + cc * fp[m]) * inv;
+                T cv[D], c2 = 0;
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    cv[d] = u[d] - U[d];
+                    c2 += cv[d] * cv[d];
+                }
+                const T we = wk * (c2 * fn[0][j] + (NC == 2 ? fn[NC - 1][j] : T(0)));
+#pragma unroll
+                for (int d = 0; d < D; ++d) blk[d] += cv[d] * we;
+            }
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                V4 v;
+                v.x = fn[m][0];
+                v.y = fn[m][1];
+                v.z = fn[m][2];
+                v.w = fn[m][3];
+                *reinterpret_cast<V4 *>(dc.f_cur + (size_t)c * rs + (size_t)m * dc.nvp + k0) = v;
+            }
         }
+        if constexpr (F32) {
+            if (++nblk == SUM_BLOCK / 4 || k00 + 128 >= dc.nvp) {
+                acc += block_to_fp64<NP>(blk);
 #pragma unroll
-        for (int m = 0; m < NC; ++m) {
-            V4 v;
-            v.x = fn[m][0];
-            v.y = fn[m][1];
-            v.z = fn[m][2];
-            v.w = fn[m][3];
-            *reinterpret_cast<V4 *>(dc.f_cur + (size_t)c * rs + (size_t)m * dc.nvp + k0) = v;
+                for (int d = 0; d < NP; ++d) blk[d] = 0;
+                nblk = 0;
+            }
         }
     }
-    for (int d = 0; d < D; ++d) {
-        const double s = warp_sum(acc[d].value());
-        if (lane == 0) dc.q[(size_t)c * D + d] = 0.5 * s;
+    if constexpr (F32) {
+        // lanes 16j.. (D = 2) or 8j.. (D = 3) hold component j
+        const int vi = lane >> (NP == 2 ? 4 : 3);
+        if ((lane & (NP == 2 ? 15 : 7)) == 0 && vi < D) dc.q[(size_t)c * D + vi] = 0.5 * acc;
+    } else {
+        for (int d = 0; d < D; ++d) {
+            const double sm = warp_sum(blk[d]);
+            if (lane == 0) dc.q[(size_t)c * D + d] = 0.5 * sm;
+        }
     }
 }
 
@@ -1906,7 +2017,7 @@ static cudaError_t gather_launch(const DevCase<T> &dc, size_t smem, cudaStream_t
     auto kern = k_gather<T, D, NC, TV, NTH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = dc.n_patches * dc.n_vt;
+    const int grid = dc.n_patches * dc.n_groups;
     kern<<<grid, NTH, smem, st>>>(dc);
     return cudaGetLastError();
 }
@@ -1961,8 +2072,7 @@ template <typename T, int D>
 static size_t sk_smem(const DevCase<T> &dc, int k)
 {
     // k_face_sum1_sep: prefix sums of the last axis, 2 sides x 3 powers per warp
-    // (8-byte elements: FP64, or double-float pairs in the FP32 form)
-    return k == SK_FACE_SUM1_SEP ? (size_t)SUM1_SEP_WARPS * 6 * (dc.cart_n[D - 1] + 1) * 8 : 0;
+    return k == SK_FACE_SUM1_SEP ? (size_t)SUM1_SEP_WARPS * 6 * (dc.cart_n[D - 1] + 1) * sizeof(T) : 0;
 }
 
 // one per-case kernel, for one case (cases == nullptr) or for the cases of a

