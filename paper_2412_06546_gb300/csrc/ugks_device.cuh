@@ -453,110 +453,17 @@ __device__ __forceinline__ void load_uw(const double *__restrict__ uw, int k, do
     w = b.y;
 }
 
-// Micro reconstruction of cell c at velocity index k (Sec. 3.1 Step 2):
-// least-squares slope grad = sum_j a_cj (f_j - f_c), Venkatakrishnan factor
-// phi = min over the faces of c of (D1^2 + eps^2 + 2 D1 D2) / (D1^2 + 2 D2^2 +
-// D1 D2 + eps^2), then a positivity scaling theta so that the reconstruction is
-// non-negative at every face centre and at the foot of the characteristic
-// after one step: with dmin = min(0, min_f D2_f),
+// Micro reconstruction of cell c (Sec. 3.1 Step 2) for the TV consecutive
+// velocities of this lane: least-squares slope grad = sum_j a_cj (f_j - f_c),
+// Venkatakrishnan factor phi = min over the faces of c of (D1^2 + eps^2 +
+// 2 D1 D2) / (D1^2 + 2 D2^2 + D1 D2 + eps^2), then a positivity scaling theta
+// so that the reconstruction is non-negative at every face centre and at the
+// foot of the characteristic after one step: with dmin = min(0, min_f D2_f),
 // v = f_c + phi (dmin + min(0, -dt u.grad)); theta = f_c / (f_c - v) if v < 0.
-template <typename T, int D, int NC>
-__device__ __forceinline__ void cell_slope(const DevCase<T> &dc, const T *__restrict__ f, int c, int k,
-                                           const T u[3], T g[NC][D])
-{
-    const size_t rs = (size_t)NC * dc.nvp;
-    T fi[NC], vmax[NC], vmin[NC];
-#pragma unroll
-    for (int m = 0; m < NC; ++m) {
-        fi[m] = f[(size_t)c * rs + (size_t)m * dc.nvp + k];
-        vmax[m] = vmin[m] = fi[m];
-#pragma unroll
-        for (int d = 0; d < D; ++d) g[m][d] = 0;
-    }
-    const int q0 = dc.nb_ptr[c], q1 = dc.nb_ptr[c + 1];
-    for (int q = q0; q < q1; ++q) {
-        const int id = dc.nb_id[q];
-        T fj[NC];
-        if (id >= 0) {
-#pragma unroll
-            for (int m = 0; m < NC; ++m) fj[m] = f[(size_t)id * rs + (size_t)m * dc.nvp + k];
-        } else {
-            const T *gr = dc.grec + (size_t)(-id - 1) * GREC;
-            T H = maxwell_h<T, D>(gr, u);
-            fj[0] = H;
-            if (NC == 2) fj[NC - 1] = gr[GR_NB] * H;
-        }
-        T a[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) a[d] = dc.nb_a[(size_t)q * D + d];
-#pragma unroll
-        for (int m = 0; m < NC; ++m) {
-            T df = fj[m] - fi[m];
-#pragma unroll
-            for (int d = 0; d < D; ++d) g[m][d] += a[d] * df;
-            vmax[m] = fj[m] > vmax[m] ? fj[m] : vmax[m];
-            vmin[m] = fj[m] < vmin[m] ? fj[m] : vmin[m];
-        }
-    }
-    const T e2 = dc.eps2[c];
-    // the limiter at the extreme d2 only (see cell_slope_tv)
-    T phi[NC], dmin[NC], dmax[NC];
-#pragma unroll
-    for (int m = 0; m < NC; ++m) dmin[m] = dmax[m] = T(0);
-    const int s0 = dc.cf_ptr[c], s1 = dc.cf_ptr[c + 1];
-    for (int s = s0; s < s1; ++s) {
-        T r[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) r[d] = dc.cf_r[(size_t)s * D + d];
-#pragma unroll
-        for (int m = 0; m < NC; ++m) {
-            T d2 = 0;
-#pragma unroll
-            for (int d = 0; d < D; ++d) d2 += g[m][d] * r[d];
-            dmin[m] = d2 < dmin[m] ? d2 : dmin[m];
-            dmax[m] = d2 > dmax[m] ? d2 : dmax[m];
-        }
-    }
-#pragma unroll
-    for (int m = 0; m < NC; ++m) {
-        phi[m] = T(1);
-        if (dc.limiter) {
-            auto venk = [&](T d1, T d2) {
-                const T a2 = d1 * d1 + e2;
-                const T num = a2 + T(2) * d1 * d2;
-                const T den = a2 + d2 * (T(2) * d2 + d1);
-                return den > T(0) ? fdiv(num, den) : T(1);
-            };
-            if (dmax[m] > T(0)) {
-                const T ph = venk(vmax[m] - fi[m], dmax[m]);
-                phi[m] = ph < phi[m] ? ph : phi[m];
-            }
-            if (dmin[m] < T(0)) {
-                const T ph = venk(vmin[m] - fi[m], dmin[m]);
-                phi[m] = ph < phi[m] ? ph : phi[m];
-            }
-        }
-    }
-    const T dt = dc.dtT;
-#pragma unroll
-    for (int m = 0; m < NC; ++m) {
-        T ug = 0;
-#pragma unroll
-        for (int d = 0; d < D; ++d) ug += u[d] * g[m][d];
-        const T foot = -dt * ug;
-        const T v = fi[m] + phi[m] * (dmin[m] + (foot < T(0) ? foot : T(0)));
-        T s = phi[m];
-        if (v < T(0)) s *= fi[m] > T(0) ? fdiv(fi[m], fi[m] - v) : T(0);
-#pragma unroll
-        for (int d = 0; d < D; ++d) g[m][d] *= s;
-    }
-}
-
-// cell_slope for the TV consecutive velocities of this lane: the same
-// arithmetic per velocity, with every face entry read once for all of them.
-// fl points at f_cur + the lane's first velocity; fi returns f_c.  The face
-// loops are unrolled so that the entry and neighbour loads of several faces
-// are in flight together (the pass is bound by their latency).
+// Every face entry is read once for all TV velocities.  fl points at f_cur +
+// the lane's first velocity; fi returns f_c.  The face loops are unrolled so
+// that the entry and neighbour loads of several faces are in flight together
+// (the pass is bound by their latency).
 template <typename T, int D, int NC, int TV>
 __device__ __forceinline__ void cell_slope_tv(const DevCase<T> &dc, const T *__restrict__ fl, int c,
                                               const T (&u)[3][TV], T (&g)[NC][D][TV], T (&fi)[NC][TV])

@@ -1308,49 +1308,72 @@ __device__ __forceinline__ void wall_sum_body(const DevCase<T> &dc, const int bx
     // macroscopicFlux) of the outgoing flux and of the incoming flux of the
     // unit-density wall Maxwellian over the step, so that F_w = A + rho_w B
     CSum<T> v[NR];
-    for (int k = threadIdx.x; k < dc.nvp; k += blockDim.x) {
-        T u[3] = {dc.u[0][k], dc.u[1][k], D == 3 ? dc.u[2][k] : T(0)};
-        T un = normal_velocity<T, D>(u, n);
-        T Fh = 0, Fb = 0;
-        int off = -1;
-        if (un > T(0)) {
-            T g[NC][D];
-            cell_slope<T, D, NC>(dc, dc.f_cur, c, k, u, g);
-            T hin = dc.f_cur[(size_t)c * rs + k], ug = 0;
-            for (int d = 0; d < D; ++d) {
-                hin += g[0][d] * r[d];
-                ug += u[d] * g[0][d];
-            }
-            v[0].add(dc.w[k] * un * (hin - hdt * ug));
-            Fh = dt * un * (hin - hdt * ug);
-            if (NC == 2) {
-                T bin = dc.f_cur[(size_t)c * rs + (size_t)(NC - 1) * dc.nvp + k], ugb = 0;
-                for (int d = 0; d < D; ++d) {
-                    bin += g[NC - 1][d] * r[d];
-                    ugb += u[d] * g[NC - 1][d];
-                }
-                Fb = dt * un * (bin - hdt * ugb);
-            }
-            off = 2;
-        } else if (un < T(0)) {
-            const T H = maxwell_h<T, D>(wr, u);
-            v[1].add(dc.w[k] * un * H);
-            Fh = dt * un * H;
-            Fb = wr[GR_NB] * Fh;
-            off = 2 + M;
-        }
-        if (off >= 0) {
-            const T wk = dc.w[k];
-            T u2 = 0;
-            for (int d = 0; d < D; ++d) u2 += u[d] * u[d];
-            T mom[M];
-            mom[0] = wk * Fh;
-            for (int d = 0; d < D; ++d) mom[1 + d] = wk * u[d] * Fh;
-            mom[D + 1] = T(0.5) * wk * (u2 * Fh + (NC == 2 ? Fb : T(0)));
+    // TW consecutive velocities per thread: the wall cell's limited slope
+    // (the gather's slope routine) reads each face entry once for all of them
+    constexpr int TW = 4;
+    for (int k0 = TW * threadIdx.x; k0 < dc.nvp; k0 += TW * blockDim.x) {
+        T u[3][TW], wk[TW], un[TW];
+        ldv<T, TW>(dc.u[0] + k0, u[0]);
+        ldv<T, TW>(dc.u[1] + k0, u[1]);
+        if (D == 3) ldv<T, TW>(dc.u[2] + k0, u[2]);
+        else
 #pragma unroll
-            for (int i = 0; i < M; ++i) {
-                if (off == 2) v[2 + i].add(mom[i]);
-                else v[2 + M + i].add(mom[i]);
+            for (int j = 0; j < TW; ++j) u[2][j] = T(0);
+        ldv<T, TW>(dc.w + k0, wk);
+        bool out = false;
+#pragma unroll
+        for (int j = 0; j < TW; ++j) {
+            const T uj[3] = {u[0][j], u[1][j], u[2][j]};
+            un[j] = normal_velocity<T, D>(uj, n);
+            out = out || un[j] > T(0);
+        }
+        T g[NC][D][TW], fi[NC][TW];
+        if (out) cell_slope_tv<T, D, NC, TW>(dc, dc.f_cur + k0, c, u, g, fi);
+#pragma unroll
+        for (int j = 0; j < TW; ++j) {
+            const T uj[3] = {u[0][j], u[1][j], u[2][j]};
+            T Fh = 0, Fb = 0;
+            int off = -1;
+            if (un[j] > T(0)) {
+                T hin = fi[0][j], ug = 0;
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    hin += g[0][d][j] * r[d];
+                    ug += uj[d] * g[0][d][j];
+                }
+                v[0].add(wk[j] * un[j] * (hin - hdt * ug));
+                Fh = dt * un[j] * (hin - hdt * ug);
+                if (NC == 2) {
+                    T bin = fi[NC - 1][j], ugb = 0;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        bin += g[NC - 1][d][j] * r[d];
+                        ugb += uj[d] * g[NC - 1][d][j];
+                    }
+                    Fb = dt * un[j] * (bin - hdt * ugb);
+                }
+                off = 2;
+            } else if (un[j] < T(0)) {
+                const T H = maxwell_h<T, D>(wr, uj);
+                v[1].add(wk[j] * un[j] * H);
+                Fh = dt * un[j] * H;
+                Fb = wr[GR_NB] * Fh;
+                off = 2 + M;
+            }
+            if (off >= 0) {
+                T u2 = 0;
+#pragma unroll
+                for (int d = 0; d < D; ++d) u2 += uj[d] * uj[d];
+                T mom[M];
+                mom[0] = wk[j] * Fh;
+#pragma unroll
+                for (int d = 0; d < D; ++d) mom[1 + d] = wk[j] * uj[d] * Fh;
+                mom[D + 1] = T(0.5) * wk[j] * (u2 * Fh + (NC == 2 ? Fb : T(0)));
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    if (off == 2) v[2 + i].add(mom[i]);
+                    else v[2 + M + i].add(mom[i]);
+                }
             }
         }
     }
@@ -1824,18 +1847,29 @@ __device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx)
     for (int d = 0; d < NP; ++d) blk[d] = 0;
     double acc = 0.0;
     int nblk = 0;
+    // the f~ vectors of the next iteration are loaded before this one's
+    // arithmetic, so that a warp keeps a load in flight while it computes
+    const T *frow = dc.f_nxt + (size_t)c * rs;
+    V4 nxt[NC];
+    if (4 * lane < dc.nvp)
+#pragma unroll
+        for (int m = 0; m < NC; ++m) nxt[m] = *reinterpret_cast<const V4 *>(frow + (size_t)m * dc.nvp + 4 * lane);
     for (int k00 = 0; k00 < dc.nvp; k00 += 128) {          // uniform over the warp
         const int k0 = k00 + 4 * lane;
         if (k0 < dc.nvp) {
             T ft[NC][4], fn[NC][4];
 #pragma unroll
             for (int m = 0; m < NC; ++m) {
-                const V4 v = *reinterpret_cast<const V4 *>(dc.f_nxt + (size_t)c * rs + (size_t)m * dc.nvp + k0);
+                const V4 v = nxt[m];
                 ft[m][0] = v.x;
                 ft[m][1] = v.y;
                 ft[m][2] = v.z;
                 ft[m][3] = v.w;
             }
+            if (k0 + 128 < dc.nvp)
+#pragma unroll
+                for (int m = 0; m < NC; ++m)
+                    nxt[m] = *reinterpret_cast<const V4 *>(frow + (size_t)m * dc.nvp + k0 + 128);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int k = k0 + j;

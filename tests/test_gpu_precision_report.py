@@ -16,8 +16,11 @@ the full-size cases (q there against its scale), 1e-4 on converged fields.
   sample cells, against the oracle stepping their local problem;
 - the Mach-5 cylinder on 2,000 cells with the 60 x 50 velocity grid, run to
   residual 1e-6 by the FP64 path (which matches the oracle to 1e-12 every
-  step) and by the FP32 form: converged fields within 1e-4.
+  step) and by the FP32 form: converged fields within 1e-4;
+- the same at full size (30k cells), run only with UGKS_LONG=1.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -161,6 +164,32 @@ def test_cylinder_converged_fp32_against_fp64():
     f64, W64 = g64.state()
     f32, W32 = g32.state()
     e = _report("cylinder2k_v60x50_converged_fp32_vs_fp64", 2, W32, g32.heat_flux(), f32, W64, g64.heat_flux(), f64)
+    g64.close()
+    g32.close()
+    assert max(m for m, _ in e.values()) <= 1e-4, e
+
+
+@pytest.mark.skipif(os.environ.get("UGKS_LONG") != "1", reason="about 10 GPU-minutes; set UGKS_LONG=1")
+def test_cylinder30k_converged_fp32_against_fp64():
+    """Config 2 at full size (30,187 cells, 60 x 50 velocities, Mach 5, Kn 0.1):
+    the FP32 form runs 20,000 steps from the blended start (residual about
+    3e-6), hands its state to the FP64 path, and both continue until the
+    residual falls below 1e-6 (the FP64 path alone would need about 25,000
+    steps at 92 ms).  Converged fields within 1e-4."""
+    case = cs.cylinder_case()
+    g32 = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP32)
+    g32.step(20000)
+    f, W = g32.state()
+    g64 = _lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=_lib.FP64)
+    g64.set_state(f, W)
+    n64, r64 = _to_convergence(g64, 1e-6, 500, 20000)
+    n32, r32 = _to_convergence(g32, 1e-6, 500, 20000)
+    print(f"CONVERGED cylinder30k_v60x50 from step 20000: fp64 +{n64} steps residual {r64:.2e}, "
+          f"fp32 +{n32} steps residual {r32:.2e}")
+    assert r64 < 1e-6 and r32 < 1e-6, (n64, r64, n32, r32)
+    f64, W64 = g64.state()
+    f32, W32 = g32.state()
+    e = _report("cylinder30k_v60x50_converged_fp32_vs_fp64", 2, W32, g32.heat_flux(), f32, W64, g64.heat_flux(), f64)
     g64.close()
     g32.close()
     assert max(m for m, _ in e.values()) <= 1e-4, e
