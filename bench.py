@@ -36,6 +36,10 @@ CYLINDER = "cylinder_Ma5_Kn0.1_tri30k_v60x50"
 E2E_MAX_BYTES = 32e9      # largest host copy of f the e2e leg stages in pinned memory
 LARGE_CVU = 2e9           # cases above this many cell-velocities get a fixed FP64 tiling
 X38_SMALL_H0 = 0.2        # first layer of the X38-like mesh for the ~100k-cell profiling instance
+# gather tiling (patch cells, velocity tile, threads per CTA, tile group) of the benchmark's workloads:
+# the autotuner's choice on GB300 (it varies between near-equal tile groups from run to run), fixed so
+# that the committed ncu traffic figure applies and no trial launches run before the timed steps
+BENCH_TILING = {WORKLOAD: (48, 64, 512, 64), CYLINDER: (48, 64, 512, 8)}
 
 
 def _peaks():
@@ -418,10 +422,13 @@ def _measure(torch, lib, name, case, args, dist, ws, local, steps, warmup, strea
     FP32 ceiling, and (e2e) the same metric through the public API with host
     buffers."""
     import numpy as np
+    tiling = (args.patch, args.vtile, args.threads, args.tile_group)
+    if not any(tiling) and name in BENCH_TILING:
+        tiling = BENCH_TILING[name]
     with torch.cuda.stream(stream):
         g = lib.Case(case["mesh"], case["vgrid"], case["params"], case["init"], precision=lib.FP32,
-                     stream=stream.cuda_stream, patch_cells=args.patch, vtile=args.vtile,
-                     threads=args.threads, tile_group=args.tile_group)
+                     stream=stream.cuda_stream, patch_cells=tiling[0], vtile=tiling[1],
+                     threads=tiling[2], tile_group=tiling[3])
     info = g.info()
     C, Nv, nc = info["n_cells"], info["nv"], info["ncomp"]
     ms, groups, clocks = _time_steps(torch, g, steps, warmup, dist, local)
