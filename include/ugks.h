@@ -162,6 +162,18 @@ ugks_status ugks_step(ugks_case *c, int32_t nsteps);
  * non-finite value or a non-positive density or temperature. */
 ugks_status ugks_check(ugks_case *c);
 
+/* Smallest and largest density of the current state over the own cells (all
+ * cells unless ugks_set_owned limited them): range[0] = min rho, range[1] =
+ * max rho (host buffer of 2 doubles); a non-positive or non-finite density
+ * counts as 0, and both are 0 for a case without own cells.  The ratio
+ * range[0] / range[1] bounds where the FP32-storage form holds its accuracy:
+ * a cell far thinner than its surroundings receives flux terms whose FP32
+ * rounding is of the order of 6e-8 times the surrounding density, so its
+ * relative error grows as 6e-8 / (range[0] / range[1]) (near-vacuum regions,
+ * e.g. behind a body after an impulsive start).  Synchronises the case
+ * stream. */
+ugks_status ugks_density_range(ugks_case *c, double *range);
+
 /* Macroscopic fields of the current state into host buffers (any may be NULL):
  * rho[C], U[C][dim], T[C], q[C][dim] (heat flux of f, Sec. 2.1).  Cell order is
  * the caller's mesh order.  Synchronises the case stream. */

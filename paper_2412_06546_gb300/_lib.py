@@ -91,6 +91,7 @@ EXPORTS = {
                                ct.c_void_p, ct.POINTER(ct.c_void_p)]),
     "ugks_step": (ct.c_int, [ct.c_void_p, ct.c_int32]),
     "ugks_check": (ct.c_int, [ct.c_void_p]),
+    "ugks_density_range": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
     "ugks_moments": (ct.c_int, [ct.c_void_p, D_P, D_P, D_P, D_P]),
     "ugks_residual": (ct.c_int, [ct.c_void_p, D_P]),
     "ugks_get_state": (ct.c_int, [ct.c_void_p, D_P, D_P]),
@@ -260,6 +261,12 @@ class Case:
 
     def check(self):
         check(load().ugks_check(self._h))
+
+    def density_range(self):
+        """(min rho, max rho) over the own cells of the current state."""
+        r = np.zeros(2)
+        check(load().ugks_density_range(self._h, r.ctypes.data))
+        return float(r[0]), float(r[1])
 
     def info(self):
         i = Info()

@@ -67,6 +67,7 @@ struct ugks_case {
     std::vector<double> wall_n_h;         // [NW][D] its normal
     double *res_d = nullptr;       // [M]
     int *flags_d = nullptr;
+    unsigned long long *range_d = nullptr;   // [2] bit patterns of the min and max density
     int n_res_blocks = 0;
     bool stepped = false;
     // kernel-group profiling
@@ -1121,6 +1122,7 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
         c->cfg.n_res_blocks = c->n_res_blocks;
         c->flags_d = (int *)c->dalloc(sizeof(int));
         cuda_ok(cudaMemsetAsync(c->flags_d, 0, sizeof(int), c->stream), "memset");
+        c->range_d = (unsigned long long *)c->dalloc(2 * sizeof(unsigned long long));
         c->res_d = (double *)c->dalloc(8 * sizeof(double));
         cuda_ok(cudaMemsetAsync(c->res_d, 0, 8 * sizeof(double), c->stream), "memset");
         c->perm_h.assign(h.perm_u2i.begin(), h.perm_u2i.end());
@@ -1176,6 +1178,22 @@ ugks_status ugks_check(ugks_case *c)
         cuda_ok(cudaMemcpyAsync(&flag, c->flags_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "check copy");
         cuda_ok(cudaStreamSynchronize(c->stream), "check sync");
         if (flag) fail(UGKS_ENUMERIC, "non-finite or non-positive density / temperature in the state");
+    });
+}
+
+ugks_status ugks_density_range(ugks_case *c, double *range)
+{
+    return guard([&] {
+        if (!c || !range) fail(UGKS_EINVAL, "case and range must not be NULL");
+        const int M = c->D + 2;
+        const double *W = c->prec == UGKS_FP64 ? c->d64.W : c->d32.W;
+        cuda_ok(ugks::launch_density_range(W, (int)c->C, M, c->owned_d, c->range_d, c->stream), "range launch");
+        unsigned long long b[2];
+        cuda_ok(cudaMemcpyAsync(b, c->range_d, sizeof(b), cudaMemcpyDeviceToHost, c->stream), "range copy");
+        cuda_ok(cudaStreamSynchronize(c->stream), "range sync");
+        if (b[0] == ~0ull) b[0] = 0ull;          // no own cell
+        std::memcpy(&range[0], &b[0], sizeof(double));
+        std::memcpy(&range[1], &b[1], sizeof(double));
     });
 }
 

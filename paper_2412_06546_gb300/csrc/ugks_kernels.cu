@@ -2007,6 +2007,32 @@ __global__ void k_check(const double *W, int n, int M, int *flags)
     if (bad) atomicOr(flags, 1);
 }
 
+// Smallest and largest density over the own cells (owned == NULL: all cells).
+// Densities are positive doubles, whose bit patterns order as the values do;
+// a non-positive or non-finite density enters as +0.  range[0] starts at all
+// ones (atomicMin), range[1] at zero (atomicMax).
+__global__ void k_density_range(const double *W, int n, int M, const unsigned char *owned,
+                                unsigned long long *range)
+{
+    unsigned long long lo = ~0ull, hi = 0ull;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        if (owned && !owned[c]) continue;
+        const double r = W[(size_t)c * M];
+        const unsigned long long b = (r > 0.0 && isfinite(r)) ? (unsigned long long)__double_as_longlong(r) : 0ull;
+        lo = b < lo ? b : lo;
+        hi = b > hi ? b : hi;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        lo = l2 < lo ? l2 : lo;
+        hi = h2 > hi ? h2 : hi;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&range[0], lo);
+        atomicMax(&range[1], hi);
+    }
+}
+
 // ------------------------------------------------------------ halo exchange
 // Rows of the halo buffer: f of the cell in the storage type [NC][nv], padded
 // to 8 bytes, then W [D+2] and q [D] in FP64.  One block per listed cell.
@@ -2397,6 +2423,16 @@ cudaError_t launch_check(const double *W, int C, int M, int *flags, cudaStream_t
 {
     if (C == 0) return cudaSuccess;
     k_check<<<cdiv(C, 128), 128, 0, st>>>(W, C, M, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density_range(const double *W, int C, int M, const unsigned char *owned,
+                                 unsigned long long *range, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(&range[0], 0xff, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&range[1], 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || C == 0) return e;
+    k_density_range<<<std::min(cdiv(C, 256), 1024), 256, 0, st>>>(W, C, M, owned, range);
     return cudaGetLastError();
 }
 

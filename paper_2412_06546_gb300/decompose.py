@@ -206,6 +206,12 @@ class DecomposedCase:
         M = self.D + 2
         return np.sqrt(tot[:M]) / np.sqrt(tot[M:])
 
+    def density_range(self):
+        """(min rho, max rho) over the whole mesh: each subdomain reports its
+        own cells (across ranks: an all-reduce MIN and MAX of these)."""
+        r = [c.density_range() for c in self.cases]
+        return min(a for a, _ in r), max(b for _, b in r)
+
     def close(self):
         for c in self.cases:
             c.close()
