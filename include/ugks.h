@@ -159,10 +159,7 @@ ugks_status ugks_create(const ugks_mesh *mesh, const ugks_vgrid *vgrid, const ug
 ugks_status ugks_step(ugks_case *c, int32_t nsteps);
 
 /* Wait for the case stream and report UGKS_ENUMERIC if the state holds a
- * non-finite value or a non-positive density or temperature, UGKS_ETIMEOUT if
- * a bounded wait inside a step ran out (the collision pass waits at most one
- * second for each bulk copy of f~; the state is then not valid).  Both stay
- * reported until the case is destroyed. */
+ * non-finite value or a non-positive density or temperature. */
 ugks_status ugks_check(ugks_case *c);
 
 /* Smallest and largest density of the current state over the own cells (all
@@ -174,18 +171,12 @@ ugks_status ugks_check(ugks_case *c);
  * surrounding gas's size, and the FP32 rounding of the stored f there is an
  * absolute error of about 6e-8 times that size.  On an impulsive Mach-5
  * cylinder start (a near-vacuum wake) the temperature error of the thinnest
- * cell measured about 0.4 * 6e-8 / ratio up to ratios near 1e-7 and grew
- * faster below, until the state was lost.  A case below its bound moves to
- * FP64 storage through ugks_get_state / ugks_set_state (exact).
+ * cell stayed below 5e-9 / ratio down to ratios of 5e-9, and the state was
+ * lost at 1.5e-9: a ratio of at least 5e-6 keeps that error below 1e-3, of
+ * 5e-5 below 1e-4.  A case below its bound moves to FP64 storage through
+ * ugks_get_state / ugks_set_state (exact).
  * Synchronises the case stream. */
 ugks_status ugks_density_range(ugks_case *c, double *range);
-
-/* Self-test of the bounded wait that guards the asynchronous copies of a step:
- * one thread waits on an mbarrier phase that nothing completes, giving up after
- * limit_ns nanoseconds of the global timer.  *completed = 0 and *elapsed_ns >=
- * limit_ns when the bound works; the GPU stays usable either way.  Uses the
- * current device and the legacy default stream; allocates 16 bytes. */
-ugks_status ugks_selftest_wait(int64_t limit_ns, int32_t *completed, int64_t *elapsed_ns);
 
 /* Macroscopic fields of the current state into host buffers (any may be NULL):
  * rho[C], U[C][dim], T[C], q[C][dim] (heat flux of f, Sec. 2.1).  Cell order is

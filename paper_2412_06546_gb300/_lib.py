@@ -92,7 +92,6 @@ EXPORTS = {
     "ugks_step": (ct.c_int, [ct.c_void_p, ct.c_int32]),
     "ugks_check": (ct.c_int, [ct.c_void_p]),
     "ugks_density_range": (ct.c_int, [ct.c_void_p, ct.c_void_p]),
-    "ugks_selftest_wait": (ct.c_int, [ct.c_int64, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int64)]),
     "ugks_moments": (ct.c_int, [ct.c_void_p, D_P, D_P, D_P, D_P]),
     "ugks_residual": (ct.c_int, [ct.c_void_p, D_P]),
     "ugks_get_state": (ct.c_int, [ct.c_void_p, D_P, D_P]),
@@ -188,14 +187,6 @@ def make_structs(mesh, vgrid, params, init=None, precision=FP64, patch_cells=0, 
                _p(wT), _p(wU), inf["rho"], (ct.c_double * 3)(*iU), inf["T"], int(precision), _p(ini),
                int(patch_cells), int(vtile), int(threads), int(tile_group), int(params.get("w0_analytic", 0)))
     return (m, v, p), keep
-
-
-def selftest_wait(limit_ns):
-    """ugks_selftest_wait: (completed, elapsed_ns) of a bounded wait on a phase
-    that nothing completes."""
-    done, ns = ct.c_int32(), ct.c_int64()
-    check(load().ugks_selftest_wait(int(limit_ns), ct.byref(done), ct.byref(ns)))
-    return int(done.value), int(ns.value)
 
 
 def cfl_dt(mesh, vgrid, cfl, n_cells=None):

@@ -1825,142 +1825,23 @@ template <> struct Vec4<double> { using type = double4_32a; };
 
 // 4 consecutive velocities per lane (rows are padded to a multiple of 32, so
 // every row start is 16-byte aligned for FP32 and 32-byte aligned for FP64)
-// Stage 2 streams the f~ row of its cell through shared memory: one warp per
-// cell, the row taken in chunks of COL_CHUNK velocities, each chunk fetched by
-// a bulk copy (cp.async.bulk, completion counted in bytes on an mbarrier) that
-// lane 0 issues COL_STAGES chunks ahead.  The bytes in flight per warp are
-// (COL_STAGES - 1) chunks whatever the register budget, and the lanes read
-// their four velocities of a chunk from shared memory.  Every wait on a chunk
-// is bounded by the global timer (one second); a warp that runs out sets bit
-// 2 of the case flags, waits (bounded again) for its copies in flight and
-// returns.
-constexpr int COL_WARPS = 8;          // warps per block (256 threads)
-constexpr int COL_CHUNK = 128;        // velocities per chunk: four per lane
-template <typename T>
-constexpr int col_stages() { return sizeof(T) == 4 ? 4 : 2; }
-constexpr int COL_STAGES_MAX = 4;
-
-template <typename T, int NC>
-__host__ __device__ constexpr size_t collide_smem_bytes()
-{
-    return (size_t)COL_WARPS * col_stages<T>() * NC * COL_CHUNK * sizeof(T);
-}
-
-__device__ __forceinline__ unsigned smem_addr(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
-{
-    unsigned done;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(done)
-                 : "r"(smem_addr(bar)), "r"(parity)
-                 : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// true once the phase of the given parity has completed; false after limit_ns
-// nanoseconds of the global timer
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
-                                                  unsigned long long limit_ns = 1000000000ull)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        for (int i = 0; i < 32; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-}
-
-// The bounded wait on a phase that nothing completes (a fresh mbarrier, no
-// arrivals): out[0] = 1 if the wait reported completion, else 0; out[1] = the
-// nanoseconds it took to give up.
-__global__ void k_wait_selftest(unsigned long long limit_ns, unsigned long long *out)
-{
-    __shared__ unsigned long long bar;
-    if (threadIdx.x != 0) return;
-    mbar_init(&bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    const unsigned long long t0 = global_ns();
-    const bool done = mbar_wait_bounded(&bar, 0u, limit_ns);
-    out[1] = global_ns() - t0;
-    out[0] = done ? 1ull : 0ull;
-}
-
-// bytes from global to shared memory, completion on bar (addresses 16-byte
-// aligned, bytes a multiple of 16)
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-// lane 0 of a collision warp: chunk i of the row into stage i % S (rows are
-// padded to a multiple of 32 velocities, so every copy is a multiple of 128 bytes)
-template <typename T, int NC, int S>
-__device__ __forceinline__ void collide_issue(T *buf, unsigned long long *bar, const T *frow, int nvp, int i)
-{
-    const int k = i * COL_CHUNK;
-    const unsigned bytes = (unsigned)(min(COL_CHUNK, nvp - k) * sizeof(T));
-    T *const dst = buf + (size_t)(i % S) * NC * COL_CHUNK;
-    // the lanes' reads of this stage (ordered by __syncwarp) precede the copy's writes
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(&bar[i % S], bytes * NC);
-#pragma unroll
-    for (int m = 0; m < NC; ++m) bulk_copy_g2s(dst + m * COL_CHUNK, frow + (size_t)m * nvp + k, bytes, &bar[i % S]);
-}
-
 template <typename T, int D, int NC>
-__device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx, T *sbuf, unsigned long long *sbar)
+__device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx)
 {
     using V4 = typename Vec4<T>::type;
-    constexpr int S = col_stages<T>();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = bx * COL_WARPS + warp;
+    const int c = bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (c >= dc.C) return;
-    const int nvp = dc.nvp;
-    const size_t rs = (size_t)NC * nvp;
-    const int nch = (nvp + COL_CHUNK - 1) / COL_CHUNK;
-    T *const buf = sbuf + (size_t)warp * S * NC * COL_CHUNK;    // [S][NC][COL_CHUNK]
-    unsigned long long *const bar = sbar + warp * S;
-    const T *const frow = dc.f_nxt + (size_t)c * rs;
-    if (lane == 0) {
-        for (int st = 0; st < S; ++st) mbar_init(&bar[st], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int i = 0; i < min(S, nch); ++i) collide_issue<T, NC, S>(buf, bar, frow, nvp, i);
-    }
-    __syncwarp();
-
-    const T *kr = dc.krec + (size_t)c * CREC;
+    // the cell's record in registers: read once, not again after every store of f
+    T kr[CREC];
+#pragma unroll
+    for (int i = 0; i < CREC; ++i) kr[i] = __ldg(dc.krec + (size_t)c * CREC + i);
     const T cc = kr[CR_C];
     const T inv = kr[CR_INV];
     T U[D];
+#pragma unroll
     for (int d = 0; d < D; ++d) U[d] = kr[CR_U + d];
+    const size_t rs = (size_t)NC * dc.nvp;
     // heat-flux terms: FP64 sums in the FP64 form; blocked sums accumulated in
     // FP64 in the FP32 form (16 terms per lane per block)
     constexpr bool F32 = std::is_same<T, float>::value;
@@ -1970,24 +1851,29 @@ __device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx,
     for (int d = 0; d < NP; ++d) blk[d] = 0;
     double acc = 0.0;
     int nblk = 0;
-    int stuck = -1;                                          // the chunk whose wait ran out
-    for (int i = 0; i < nch; ++i) {                         // uniform over the warp
-        const int st = i % S;
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar[st], (unsigned)(i / S) & 1u))) {
-            stuck = i;
-            break;
-        }
-        const int k0 = i * COL_CHUNK + 4 * lane;
-        if (k0 < nvp) {
+    // the f~ vectors of the next iteration are loaded before this one's
+    // arithmetic, so that a warp keeps a load in flight while it computes
+    const T *frow = dc.f_nxt + (size_t)c * rs;
+    V4 nxt[NC];
+    if (4 * lane < dc.nvp)
+#pragma unroll
+        for (int m = 0; m < NC; ++m) nxt[m] = *reinterpret_cast<const V4 *>(frow + (size_t)m * dc.nvp + 4 * lane);
+    for (int k00 = 0; k00 < dc.nvp; k00 += 128) {          // uniform over the warp
+        const int k0 = k00 + 4 * lane;
+        if (k0 < dc.nvp) {
             T ft[NC][4], fn[NC][4];
 #pragma unroll
             for (int m = 0; m < NC; ++m) {
-                const V4 v = *reinterpret_cast<const V4 *>(buf + ((size_t)st * NC + m) * COL_CHUNK + 4 * lane);
+                const V4 v = nxt[m];
                 ft[m][0] = v.x;
                 ft[m][1] = v.y;
                 ft[m][2] = v.z;
                 ft[m][3] = v.w;
             }
+            if (k0 + 128 < dc.nvp)
+#pragma unroll
+                for (int m = 0; m < NC; ++m)
+                    nxt[m] = *reinterpret_cast<const V4 *>(frow + (size_t)m * dc.nvp + k0 + 128);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int k = k0 + j;
@@ -2014,28 +1900,17 @@ __device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx,
                 v.y = fn[m][1];
                 v.z = fn[m][2];
                 v.w = fn[m][3];
-                *reinterpret_cast<V4 *>(dc.f_cur + (size_t)c * rs + (size_t)m * nvp + k0) = v;
+                *reinterpret_cast<V4 *>(dc.f_cur + (size_t)c * rs + (size_t)m * dc.nvp + k0) = v;
             }
         }
-        __syncwarp();
-        if (lane == 0 && i + S < nch) collide_issue<T, NC, S>(buf, bar, frow, nvp, i + S);
         if constexpr (F32) {
-            if (++nblk == SUM_BLOCK / 4 || i + 1 == nch) {
+            if (++nblk == SUM_BLOCK / 4 || k00 + 128 >= dc.nvp) {
                 acc += block_to_fp64<NP>(blk);
 #pragma unroll
                 for (int d = 0; d < NP; ++d) blk[d] = 0;
                 nblk = 0;
             }
         }
-    }
-    if (stuck >= 0) {
-        // chunks stuck .. stuck + S - 1 may still be in flight
-        if (lane == 0) {
-            atomicOr(dc.flags, 2);
-            for (int j = stuck; j < min(stuck + S, nch); ++j) mbar_wait_bounded(&bar[j % S], (unsigned)(j / S) & 1u);
-        }
-        __syncwarp();
-        return;
     }
     if constexpr (F32) {
         // lanes 16j.. (D = 2) or 8j.. (D = 3) hold component j
@@ -2049,23 +1924,21 @@ __device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx,
     }
 }
 
+// five 256-thread blocks per SM in the FP32 form (48 registers; the batched
+// 2D variant would spill at that bound)
 template <typename T, int D, int NC>
-__global__ void __launch_bounds__(COL_WARPS * 32) k_collide(DevCase<T> dc)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 0) k_collide(DevCase<T> dc)
 {
-    extern __shared__ __align__(128) unsigned char col_raw[];
-    __shared__ unsigned long long col_bar[COL_WARPS * COL_STAGES_MAX];
-    collide_body<T, D, NC>(dc, blockIdx.x, reinterpret_cast<T *>(col_raw), col_bar);
+    collide_body<T, D, NC>(dc, blockIdx.x);
 }
 
 template <typename T, int D, int NC>
-__global__ void __launch_bounds__(COL_WARPS * 32) k_collide_batch(const DevCase<T> *__restrict__ cases,
-                                                                  const int *__restrict__ off, int n)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 && D == 3 ? 5 : 0)
+    k_collide_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
 {
-    extern __shared__ __align__(128) unsigned char col_raw[];
-    __shared__ unsigned long long col_bar[COL_WARPS * COL_STAGES_MAX];
     int bx;
     const DevCase<T> &dc = batch_case(cases, off, n, bx);
-    collide_body<T, D, NC>(dc, bx, reinterpret_cast<T *>(col_raw), col_bar);
+    collide_body<T, D, NC>(dc, bx);
 }
 
 // ------------------------------------------------------------ state I/O
@@ -2255,19 +2128,17 @@ static int sk_blocks(const DevCase<T> &dc, int k)
     case SK_FACE_FIN2: return faces ? cdiv(F, 64) : 0;
     case SK_WALL_SUM: return dc.NW;
     case SK_UPDATE_W: return cdiv(C, 256);
-    case SK_COLLIDE: return cdiv(C, COL_WARPS);
+    case SK_COLLIDE: return cdiv(C, 8);
     default: return 0;
     }
 }
 
-constexpr int kSkThreads[SK_COUNT] = {128, 128, 128, 32 * SUM1_SEP_WARPS, 256, 128, 256, 256, 64, 256, 256, COL_WARPS * 32};
+constexpr int kSkThreads[SK_COUNT] = {128, 128, 128, 32 * SUM1_SEP_WARPS, 256, 128, 256, 256, 64, 256, 256, 256};
 
 template <typename T, int D>
 static size_t sk_smem(const DevCase<T> &dc, int k)
 {
-    // k_face_sum1_sep: prefix sums of the last axis, 2 sides x 3 powers per warp;
-    // k_collide: the chunk stages of its warps
-    if (k == SK_COLLIDE) return collide_smem_bytes<T, D == 2 ? 2 : 1>();
+    // k_face_sum1_sep: prefix sums of the last axis, 2 sides x 3 powers per warp
     return k == SK_FACE_SUM1_SEP ? (size_t)SUM1_SEP_WARPS * 6 * (dc.cart_n[D - 1] + 1) * sizeof(T) : 0;
 }
 
@@ -2559,12 +2430,6 @@ cudaError_t launch_check(const double *W, int C, int M, int *flags, cudaStream_t
 {
     if (C == 0) return cudaSuccess;
     k_check<<<cdiv(C, 128), 128, 0, st>>>(W, C, M, flags);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned long long *out, cudaStream_t st)
-{
-    k_wait_selftest<<<1, 32, 0, st>>>(limit_ns, out);
     return cudaGetLastError();
 }
 

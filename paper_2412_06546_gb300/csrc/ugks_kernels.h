@@ -57,7 +57,6 @@ cudaError_t launch_moments_out(const double *W, const double *q, const long long
 cudaError_t launch_W_permute(const double *src, const long long *perm, int C, int D, double *dst, int to_internal,
                              cudaStream_t st);
 cudaError_t launch_check(const double *W, int C, int M, int *flags, cudaStream_t st);
-cudaError_t launch_wait_selftest(unsigned long long limit_ns, unsigned long long *out, cudaStream_t st);
 cudaError_t launch_density_range(const double *W, int C, int M, const unsigned char *owned,
                                  unsigned long long *range, cudaStream_t st);
 
