@@ -476,8 +476,14 @@ __device__ __forceinline__ void face_sum1_body(const DevCase<T> &dc, const int b
     const int lane = threadIdx.x & 31;
     constexpr int M = D + 2;
     if (f >= dc.F || dc.ftype[f] == FT_WALL) return;
-    const T *sL = dc.fside + (size_t)f * 2 * GREC;
-    const T *sR = sL + GREC;
+    // both side records in registers; a velocity selects its upwind side's
+    // values instead of loading them through a selected pointer
+    T sL[GREC], sR[GREC];
+#pragma unroll
+    for (int i = 0; i < GREC; ++i) {
+        sL[i] = __ldg(dc.fside + (size_t)f * 2 * GREC + i);
+        sR[i] = __ldg(dc.fside + (size_t)f * 2 * GREC + GREC + i);
+    }
     T n[D], Ur[D];
     for (int d = 0; d < D; ++d) {
         n[d] = dc.fn[(size_t)f * D + d];
@@ -490,7 +496,9 @@ __device__ __forceinline__ void face_sum1_body(const DevCase<T> &dc, const int b
         T un = normal_velocity<T, D>(u, n);
         T h, b;
         if (un != T(0)) {
-            const T *s = un > T(0) ? sL : sR;
+            T s[GREC];
+#pragma unroll
+            for (int i = 0; i < GREC; ++i) s[i] = un > T(0) ? sL[i] : sR[i];
             h = maxwell_h<T, D>(s, u);
             b = s[GR_NB] * h;
         } else {
