@@ -1882,11 +1882,22 @@ __device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx)
 #pragma unroll
                 for (int m = 0; m < NC; ++m)
                     nxt[m] = *reinterpret_cast<const V4 *>(frow + (size_t)m * dc.nvp + k0 + 128);
+            // the lane's four velocities from the per-component arrays: each load
+            // of the warp covers one contiguous span (the packed [k][4] records
+            // of four consecutive velocities per lane would touch four times the
+            // cache lines per load)
+            T uv[3][4], wv[4];
+            ldv<T, 4>(dc.u[0] + k0, uv[0]);
+            ldv<T, 4>(dc.u[1] + k0, uv[1]);
+            if (D == 3) ldv<T, 4>(dc.u[2] + k0, uv[2]);
+            else
+#pragma unroll
+                for (int j = 0; j < 4; ++j) uv[2][j] = T(0);
+            ldv<T, 4>(dc.w + k0, wv);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int k = k0 + j;
-                T u[3], wk;
-                load_uw(dc.uw, k, u, wk);
+                const T u[3] = {uv[0][j], uv[1][j], uv[2][j]};
+                const T wk = wv[j];
                 T fp[NC];
                 shakhov_fplus<T, D, NC>(kr, u, fp);
 #pragma unroll
@@ -1932,17 +1943,17 @@ __device__ __forceinline__ void collide_body(const DevCase<T> &dc, const int bx)
     }
 }
 
-// five 256-thread blocks per SM in the FP32 form (48 registers; the batched
-// 2D variant would spill at that bound)
+// five 256-thread blocks per SM in the 2D FP32 form (48 registers); the 3D
+// FP32 form and the batched kernels would spill at that bound
 template <typename T, int D, int NC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 0) k_collide(DevCase<T> dc)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 && D == 2 ? 5 : 0) k_collide(DevCase<T> dc)
 {
     collide_body<T, D, NC>(dc, blockIdx.x);
 }
 
 template <typename T, int D, int NC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 && D == 3 ? 5 : 0)
-    k_collide_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off, int n)
+__global__ void __launch_bounds__(256) k_collide_batch(const DevCase<T> *__restrict__ cases, const int *__restrict__ off,
+                                                       int n)
 {
     int bx;
     const DevCase<T> &dc = batch_case(cases, off, n, bx);
