@@ -49,17 +49,16 @@ constexpr int SUM1_SEP_MAX_NL = 512;
 // n = unit normal of f pointing out of c, ro = x_f - x_other (periodic image;
 // 0 for far-field ghosts), cs = -S_f / |Omega_c|.  Grouped in 16-byte vectors
 // so that each pass loads only the vectors it reads: the slopes' first face
-// loop the SLOPE1 values from SLOPE1_OFF (the vector holding a; in 2D a and
-// rs share it), their limiter loop the first vector (rs), the flux loop
-// everything but the vectors in [SKIP0, SKIP1) (a, in 3D).
+// loop the first SLOPE1 values (a, rs), their limiter loop the first vector
+// (rs), the flux loop everything but the vectors in [SKIP0, SKIP1) (a, in 3D).
 template <int D> struct GEnt;
 template <> struct GEnt<2> {
     static constexpr int A = 0, RS = 2, N = 4, RO = 6, CS = 8, LEN = 12;
-    static constexpr int SLOPE1_OFF = 0, SLOPE1 = 4, LIMIT = 4, SKIP0 = 0, SKIP1 = 0;
+    static constexpr int SLOPE1 = 4, LIMIT = 4, SKIP0 = 0, SKIP1 = 0;
 };
 template <> struct GEnt<3> {
     static constexpr int RS = 0, CS = 3, A = 4, N = 8, RO = 12, LEN = 16;
-    static constexpr int SLOPE1_OFF = 4, SLOPE1 = 4, LIMIT = 4, SKIP0 = 4, SKIP1 = 8;
+    static constexpr int SLOPE1 = 8, LIMIT = 4, SKIP0 = 4, SKIP1 = 8;
 };
 
 // Everything a kernel needs, by value.  Geometry used inside velocity loops is
@@ -470,7 +469,7 @@ __device__ __forceinline__ void cell_slope_tv(const DevCase<T> &dc, const T *__r
                                               const T (&u)[3][TV], T (&g)[NC][D][TV], T (&fi)[NC][TV])
 {
     using E = GEnt<D>;
-    constexpr int HA = E::SLOPE1;                 // the vector(s) holding a
+    constexpr int HA = E::SLOPE1;                 // a and rs, in whole vector loads
     const int nvp = dc.nvp;
     const size_t rs = (size_t)NC * nvp;
     T vmax[NC][TV], vmin[NC][TV];
@@ -491,7 +490,7 @@ __device__ __forceinline__ void cell_slope_tv(const DevCase<T> &dc, const T *__r
         const int4 gi = __ldg(dc.gi + e);
         if (gi.z == FT_WALL) continue;
         T ge[HA];
-        load_rec<HA>(dc.gf + (size_t)e * E::LEN + E::SLOPE1_OFF, ge);
+        load_rec<HA>(dc.gf + (size_t)e * E::LEN, ge);
         T fj[NC][TV];
         if (gi.z == FT_FARFIELD) {
             T gr[GREC];
@@ -514,7 +513,7 @@ __device__ __forceinline__ void cell_slope_tv(const DevCase<T> &dc, const T *__r
             for (int j = 0; j < TV; ++j) {
                 const T df = fj[m][j] - fi[m][j];
 #pragma unroll
-                for (int d = 0; d < D; ++d) g[m][d][j] += ge[E::A - E::SLOPE1_OFF + d] * df;
+                for (int d = 0; d < D; ++d) g[m][d][j] += ge[E::A + d] * df;
                 vmax[m][j] = fj[m][j] > vmax[m][j] ? fj[m][j] : vmax[m][j];
                 vmin[m][j] = fj[m][j] < vmin[m][j] ? fj[m][j] : vmin[m][j];
             }
